@@ -1,0 +1,187 @@
+/*
+ * spmv.h — C ABI of the GB300 (sm_103a) CRS sparse matrix-vector multiply.
+ *
+ * The operation is the CRS product of Sec. 1.2 of Schubert, Hager, Fehske and
+ * Wellein, "Parallel sparse matrix-vector multiplication as a test case for
+ * hybrid MPI+OpenMP programming" (arXiv 1101.0091):
+ *
+ *     C(i) = sum_{j = row_ptr(i)}^{row_ptr(i+1)-1} val(j) * B(col_idx(j))
+ *
+ * with 0-based indices.  The paper's loop accumulates into C; every apply call
+ * here OVERWRITES C (C = A*B), except where stated.  All arithmetic is FP64
+ * (products and row sums); the FP32-value option only changes how val is
+ * stored (it is widened to FP64 exactly before each multiply).
+ *
+ * Conventions
+ *  - Host pointers are plain host memory unless a name says _dev (device
+ *    memory of the plan's device) or _pinned (page-locked host memory).
+ *  - Index arrays are int32, values float64; row-major blocks of k right-hand
+ *    sides are addressed as B[col * ldb + c] and C[row * ldc + c].
+ *  - Streams are CUDA stream handles (cudaStream_t / CUstream) passed as
+ *    void*; NULL is the legacy default stream.  Apply calls are asynchronous
+ *    on the given stream and never synchronise the device.
+ *  - Every call returns an spmv_status; no call throws or aborts.  The text of
+ *    the last error of the calling thread is in spmv_last_error().
+ *  - A plan owns all device memory it allocates; the caller keeps ownership
+ *    of every array it passes.  A plan may be applied concurrently from
+ *    several streams only if the output buffers differ.
+ *  - Duplicate column indices inside a row are allowed (their products are
+ *    summed); columns need not be sorted.
+ */
+#ifndef SPMV_GB300_H
+#define SPMV_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmv_plan* spmv_handle;
+typedef struct spmv_batch_plan* spmv_batch_handle;
+typedef struct spmv_model* spmv_model_handle;
+
+typedef enum {
+  SPMV_OK = 0,
+  SPMV_ERR_ARG = 1,         /* bad argument (null pointer, negative size, k out of range, ...) */
+  SPMV_ERR_CSR = 2,         /* malformed CRS arrays (rejected on the host before any launch)   */
+  SPMV_ERR_CUDA = 3,        /* a CUDA runtime call failed; message in spmv_last_error()        */
+  SPMV_ERR_OOM = 4,         /* device or host allocation failed; nothing was leaked            */
+  SPMV_ERR_TIMEOUT = 5,     /* a bounded wait ran out (host event wait or a device-side wait)  */
+  SPMV_ERR_UNSUPPORTED = 6, /* the request needs a format or option the plan was not built for */
+  SPMV_ERR_DEVICE = 7       /* a kernel reported an error through the plan's status word        */
+} spmv_status;
+
+/* Kernel variants.  All compute the same product with FP64 accumulation and
+ * one fused multiply-add per stored entry. */
+typedef enum {
+  SPMV_VARIANT_AUTO = 0,   /* the plan's choice (cost model if attached, else CRS_STAGED)       */
+  SPMV_CRS_STAGED = 1,     /* thread per row; each CTA's contiguous val/col tile is brought     */
+                           /* into shared memory by one bulk copy (cp.async.bulk + mbarrier);   */
+                           /* rows longer than 64 go to warp-per-row blocks                      */
+  SPMV_CRS_L1 = 2,         /* L lanes per row (L = 1, 2, 4, ..., 32), loads straight from HBM,   */
+  SPMV_CRS_L2 = 3,         /* warp-shuffle reduction of the L partial sums                       */
+  SPMV_CRS_L4 = 4,
+  SPMV_CRS_L8 = 5,
+  SPMV_CRS_L16 = 6,
+  SPMV_CRS_L32 = 7,
+  SPMV_SELL = 8,           /* SELL-C-sigma, C = 32, sigma from the options / set_variant         */
+  SPMV_N_VARIANTS = 9
+} spmv_variant;
+
+typedef struct {
+  int32_t variant;      /* spmv_variant; 0 = AUTO                                               */
+  int32_t sell_sigma;   /* sigma of SPMV_SELL (sorting window); <= 1 means no sorting           */
+  int32_t val_fp32;     /* 1: store val as float32 (exactly widened to FP64 before each FMA)    */
+  int32_t max_k;        /* largest k for spmv_apply_block (1..16); 0 means 16                   */
+  int64_t halo_begin;   /* >= 0: build the local/halo column split at column h (Sec. 3.1);     */
+                        /* -1: no split.  A zero-initialised struct is NOT the default: use     */
+                        /* spmv_default_options().                                               */
+} spmv_options;
+
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  int32_t variant;          /* active variant                                                   */
+  int32_t sell_sigma;       /* sigma of the built SELL arrays (0 if none)                       */
+  int64_t sell_slots;       /* stored SELL slots, sum of 32 * chunk_len (0 if none)             */
+  int64_t sell_chunks;      /* number of SELL chunks                                            */
+  int64_t n_halo_rows;      /* rows with at least one halo entry (split plans; else 0)          */
+  int64_t halo_nnz;         /* entries with col >= halo_begin                                   */
+  int64_t n_row_blocks;     /* CTAs of CRS_STAGED (row blocks)                                  */
+  int32_t tile_nnz;         /* nonzero capacity of one CRS_STAGED tile                          */
+  int32_t val_fp32;
+  int64_t device_bytes;     /* device memory held by the plan                                   */
+} spmv_info;
+
+/* Default options: AUTO, sigma 1, FP64 values, max_k 16, no split. */
+spmv_options spmv_default_options(void);
+
+/* Thread-local text of the last error ("" if none). */
+const char* spmv_last_error(void);
+
+/* Create a plan on the current CUDA device from HOST CRS arrays (copied;
+ * the caller keeps them).  row_ptr has n_rows+1 entries with row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n_rows] = nnz <= 2^31-1; 0 <= col_idx < n_cols.
+ * Violations return SPMV_ERR_CSR before anything is allocated on the device.
+ * Sec. 1.2 (CRS format).  opt may be NULL (defaults). */
+spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols,
+                        const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                        const spmv_options* opt);
+
+/* Free all memory of a plan; NULL is accepted.  Synchronises the device first. */
+spmv_status spmv_destroy(spmv_handle h);
+
+/* C_dev[0:n_rows] = A * B_dev[0:n_cols] (overwrite), asynchronous on stream.
+ * Sec. 1.2 listing. */
+spmv_status spmv_apply(spmv_handle h, const double* B_dev, double* C_dev, void* stream);
+
+/* Block of k right-hand sides (SpMM): C_dev[i*ldc + c] = sum_j val(j) * B_dev[col(j)*ldb + c]
+ * for c < k; 1 <= k <= opt.max_k <= 16, ldb >= k, ldc >= k.  Same loop as
+ * Sec. 1.2, applied to k vectors at once. */
+spmv_status spmv_apply_block(spmv_handle h, const double* B_dev, int32_t k, int64_t ldb,
+                             double* C_dev, int64_t ldc, void* stream);
+
+/* Local/halo split product with overlapped halo copy (Sec. 3.1 and 3.2 recast
+ * for one GPU): on copy_stream, B_halo_pinned[0 : n_cols - h] is copied into
+ * B_dev[h : n_cols] while the local kernel (entries with col < h) writes C on
+ * main_stream; main_stream then waits for the copy and the halo kernel adds
+ * the entries with col >= h into C.  B_dev[0:h] must already hold the local
+ * part.  Requires a plan built with halo_begin = h.  copy_stream may equal
+ * main_stream (no overlap).  On return all work is enqueued; main_stream
+ * carries the completion of both. */
+spmv_status spmv_apply_split(spmv_handle h, double* B_dev, const double* B_halo_pinned,
+                             double* C_dev, void* main_stream, void* copy_stream);
+
+/* Same product, end to end from HOST buffers: B_host (n_cols*k) is copied to
+ * plan-owned device buffers, multiplied, and C_host (n_rows*k, ldc = k) is
+ * copied back; synchronises the stream before returning.  k = 1 uses
+ * spmv_apply, k > 1 spmv_apply_block with ldb = ldc = k. */
+spmv_status spmv_apply_host(spmv_handle h, const double* B_host, int32_t k, double* C_host,
+                            void* stream);
+
+/* Switch the active variant (building its format on first use: the row
+ * blocks of CRS_STAGED, or SELL-C-sigma with the given sigma). */
+spmv_status spmv_set_variant(spmv_handle h, int32_t variant, int32_t sell_sigma);
+
+spmv_status spmv_get_info(spmv_handle h, spmv_info* info);
+
+/* Wait for the plan's work on `stream`, then read and clear the plan's device
+ * status word: SPMV_ERR_DEVICE (message names the failing step) if a kernel
+ * reported a failed bounded wait, else SPMV_OK. */
+spmv_status spmv_check(spmv_handle h, void* stream);
+
+/* Copy the built SELL-C-sigma arrays to host arrays sized from spmv_info:
+ * perm[n_rows], chunk_ptr[sell_chunks+1], chunk_len[sell_chunks],
+ * sell_col[sell_slots], sell_val[sell_slots] (any may be NULL to skip).
+ * Layout: chunks of C = 32 sorted rows, column-major inside a chunk. */
+spmv_status spmv_sell_export(spmv_handle h, int32_t* perm, int64_t* chunk_ptr, int32_t* chunk_len,
+                             int32_t* sell_col, double* sell_val);
+
+/* Copy the local/halo split arrays to host arrays sized from spmv_info:
+ * loc_row_ptr[n_rows+1], loc_col/loc_val[nnz - halo_nnz], halo_rows[n_halo_rows],
+ * halo_row_ptr[n_halo_rows+1], halo_col/halo_val[halo_nnz] (any may be NULL). */
+spmv_status spmv_split_export(spmv_handle h, int32_t* loc_row_ptr, int32_t* loc_col, double* loc_val,
+                              int32_t* halo_rows, int32_t* halo_row_ptr, int32_t* halo_col,
+                              double* halo_val);
+
+/* ----------------------------------------------------------------------------
+ * Matrix features read by the cost model (host computation, no device use).
+ * out[34] (float64) for HOST CRS arrays and k right-hand sides:
+ *   [0:13]  fraction of rows in length bin b: b(L) = 0 for L = 0, else
+ *           min(1 + floor(log2 L), 12) (bin 12 holds L >= 2048)
+ *   [13:26] fraction of nonzeros in the rows of bin b
+ *   [26] log2(1 + n_rows)      [27] log2(1 + nnz)        [28] nnz / n_rows (Nnzr)
+ *   [29] log2(1 + max L)       [30] std(L) / (1 + Nnzr)  [31] max |i - j| / n_cols
+ *   [32] mean over non-empty rows of (max col - min col) / n_cols
+ *   [33] log2(k)
+ * Row-length statistics and the bandwidth follow the paper's discussion of
+ * Nnzr and of B-access locality (Sec. 1.2, Sec. 2).  Malformed CRS -> SPMV_ERR_CSR.
+ * ------------------------------------------------------------------------- */
+spmv_status spmv_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
+                          int32_t k, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_GB300_H */

@@ -1,0 +1,136 @@
+"""GB300 (sm_103a) CRS sparse matrix-vector multiply C = A*B.
+
+The compute path is the C ABI library built from ``csrc/`` (see
+``include/spmv.h``); this package only marshals arguments into it.  PyTorch is
+used by callers for device memory and streams; nothing here computes on the
+host.
+
+    from paper_1101_0091_gb300 import Plan
+    plan = Plan(n_rows, n_cols, row_ptr, col_idx, val)     # host numpy arrays
+    plan.apply(B, C)                                       # torch CUDA float64 tensors
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as _b
+from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_block, spmv_apply_host,  # noqa: F401
+                       spmv_apply_split, spmv_check, spmv_create, spmv_default_options, spmv_destroy,
+                       spmv_get_info, spmv_last_error, spmv_options, spmv_sell_export, spmv_set_variant,
+                       spmv_split_export, spmv_features, SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
+                       SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_N_VARIANTS)
+
+LANE_VARIANTS = {1: SPMV_CRS_L1, 2: SPMV_CRS_L2, 4: SPMV_CRS_L4, 8: SPMV_CRS_L8, 16: SPMV_CRS_L16,
+                 32: SPMV_CRS_L32}
+
+
+N_FEATURES = 34
+
+
+def features(A, k: int = 1) -> np.ndarray:
+    """Cost-model feature vector of a host CRS matrix (computed by the library)."""
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    out = np.empty(N_FEATURES, dtype=np.float64)
+    spmv_features(A.n_rows, A.n_cols, rp.ctypes.data, ci.ctypes.data, k, out.ctypes.data)
+    return out
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class Plan:
+    """Owns one spmv_handle.  Host CRS arrays are copied at construction."""
+
+    def __init__(self, n_rows: int, n_cols: int, row_ptr, col_idx, val, *, variant: int = SPMV_VARIANT_AUTO,
+                 sell_sigma: int = 1, val_fp32: bool = False, max_k: int = 16, halo_begin: int = -1):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        va = np.ascontiguousarray(val, dtype=np.float64)
+        o = spmv_default_options()
+        o.variant, o.sell_sigma, o.val_fp32, o.max_k, o.halo_begin = variant, sell_sigma, int(val_fp32), max_k, halo_begin
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.handle = spmv_create(n_rows, n_cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, o)
+
+    @classmethod
+    def from_csr(cls, A, **kw) -> "Plan":
+        return cls(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.val, **kw)
+
+    def apply(self, B, C, stream=None) -> None:
+        spmv_apply(self.handle, _ptr(B), _ptr(C), _stream_handle(stream))
+
+    def apply_block(self, B, C, k: int | None = None, stream=None) -> None:
+        """B: (n_cols, ldb) row-major, C: (n_rows, ldc) row-major; k defaults to B.shape[1]."""
+        k = B.shape[1] if k is None else k
+        spmv_apply_block(self.handle, _ptr(B), k, B.stride(0), _ptr(C), C.stride(0), _stream_handle(stream))
+
+    def apply_split(self, B, B_halo_pinned, C, main_stream=None, copy_stream=None) -> None:
+        ms = _stream_handle(main_stream)
+        cs = ms if copy_stream is None else _stream_handle(copy_stream)
+        spmv_apply_split(self.handle, _ptr(B), _ptr(B_halo_pinned), _ptr(C), ms, cs)
+
+    def apply_host(self, B: np.ndarray, k: int = 1, stream=None) -> np.ndarray:
+        """End to end from host memory: copies B in, multiplies, copies C back (synchronous)."""
+        Bc = np.ascontiguousarray(B, dtype=np.float64)
+        C = np.empty((self.n_rows, k) if k > 1 else self.n_rows, dtype=np.float64)
+        spmv_apply_host(self.handle, Bc.ctypes.data, k, C.ctypes.data, _stream_handle(stream))
+        return C
+
+    def apply_host_ptr(self, B_ptr: int, k: int, C_ptr: int, stream=None) -> None:
+        spmv_apply_host(self.handle, B_ptr, k, C_ptr, _stream_handle(stream))
+
+    def set_variant(self, variant: int, sell_sigma: int = 1) -> None:
+        spmv_set_variant(self.handle, variant, sell_sigma)
+
+    def info(self):
+        return spmv_get_info(self.handle)
+
+    def check(self, stream=None) -> None:
+        spmv_check(self.handle, _stream_handle(stream))
+
+    def sell_export(self) -> dict:
+        i = self.info()
+        out = {"perm": np.empty(i.n_rows, np.int32), "chunk_ptr": np.empty(i.sell_chunks + 1, np.int64),
+               "chunk_len": np.empty(i.sell_chunks, np.int32), "sell_col": np.empty(i.sell_slots, np.int32),
+               "sell_val": np.empty(i.sell_slots, np.float64)}
+        spmv_sell_export(self.handle, *(out[k].ctypes.data for k in ("perm", "chunk_ptr", "chunk_len", "sell_col",
+                                                                     "sell_val")))
+        return out
+
+    def split_export(self) -> dict:
+        i = self.info()
+        nl = i.nnz - i.halo_nnz
+        out = {"loc_row_ptr": np.empty(i.n_rows + 1, np.int32), "loc_col": np.empty(nl, np.int32),
+               "loc_val": np.empty(nl, np.float64), "halo_rows": np.empty(i.n_halo_rows, np.int32),
+               "halo_row_ptr": np.empty(i.n_halo_rows + 1, np.int32), "halo_col": np.empty(i.halo_nnz, np.int32),
+               "halo_val": np.empty(i.halo_nnz, np.float64)}
+        keys = ("loc_row_ptr", "loc_col", "loc_val", "halo_rows", "halo_row_ptr", "halo_col", "halo_val")
+        spmv_split_export(self.handle, *(out[k].ctypes.data for k in keys))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None:
+            spmv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

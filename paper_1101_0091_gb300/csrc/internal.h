@@ -1,0 +1,119 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spmv.h"
+
+namespace spmv {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+spmv_status fail(spmv_status st, const std::string& msg);
+spmv_status cuda_fail(cudaError_t e, const char* what);
+
+#define SPMV_CUDA(call)                                                   \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) return ::spmv::cuda_fail(e_, #call);           \
+  } while (0)
+
+// Device status word codes written by kernels (0 = fine).
+enum : int { DEV_OK = 0, DEV_WAIT_TIMEOUT = 1 };
+
+// Bounded device waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+// ------------------------------------------------------- layout constants
+constexpr int kThreads = 256;        // threads per CTA of the row kernels
+constexpr int kStagedRows = 256;     // rows per CRS_STAGED block (one per thread)
+constexpr int kLongRow = 64;         // rows longer than this are handled warp-per-row
+constexpr int kWarpRowsPerBlock = kThreads / 32;
+constexpr int kSellC = 32;           // SELL chunk height
+constexpr uint32_t kBlockWarpFlag = 0x80000000u;  // high bit of a row-block entry: warp-per-row block
+
+// ------------------------------------------------------- device buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct HostCsr {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  std::vector<int32_t> row_ptr, col;
+  std::vector<double> val;
+};
+
+struct SellHost {
+  int64_t C = kSellC, sigma = 1, n_chunks = 0, slots = 0;
+  std::vector<int32_t> perm, chunk_len, col;
+  std::vector<int64_t> chunk_ptr;
+  std::vector<double> val;
+};
+
+struct SplitHost {
+  int64_t h = -1;
+  std::vector<int32_t> loc_row_ptr, loc_col, halo_rows, halo_row_ptr, halo_col;
+  std::vector<double> loc_val, halo_val;
+};
+
+// Device view of one CRS matrix (values in FP64 and, optionally, FP32).
+struct CsrDev {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;     // padded to a multiple of 4 entries + 4
+  const double* val = nullptr;      // padded to a multiple of 2 entries + 2
+  const float* val32 = nullptr;     // padded to a multiple of 4 entries + 4
+  const uint32_t* blk = nullptr;    // row blocks of CRS_STAGED (n_blk + 1 entries)
+  int64_t n_blk = 0;
+  int tile = 0;                     // nonzero capacity of a CRS_STAGED tile
+};
+
+struct SellDev {
+  int64_t n_rows = 0, n_chunks = 0, slots = 0;
+  int sigma = 0;
+  const int32_t* perm = nullptr;
+  const int64_t* chunk_ptr = nullptr;
+  const int32_t* chunk_len = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  const float* val32 = nullptr;
+};
+
+// Halo part of a split: rows listed in `rows`, CRS over them.
+struct HaloDev {
+  int64_t n_rows = 0, nnz = 0;
+  const int32_t* rows = nullptr;
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  const float* val32 = nullptr;
+};
+
+// ------------------------------------------------------- host builders
+bool validate_csr(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
+                  std::string* why);
+std::vector<uint32_t> build_row_blocks(const int32_t* row_ptr, int64_t n_rows, int rows_per_block,
+                                       int long_row, int* tile_out);
+void build_sell(const HostCsr& A, int64_t C, int64_t sigma, SellHost* out);
+void build_split(const HostCsr& A, int64_t h, SplitHost* out);
+void compute_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
+                      int k, double* f);
+
+// ------------------------------------------------------- kernel launchers
+// All launchers enqueue on `stream` and return the launch error (if any).
+cudaError_t launch_crs_staged(const CsrDev& A, bool fp32, const double* B, int64_t ldb, double* C,
+                              int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s);
+cudaError_t launch_crs_lanes(const CsrDev& A, bool fp32, int lanes, const double* B, int64_t ldb,
+                             double* C, int64_t ldc, int k, cudaStream_t s);
+cudaError_t launch_sell(const SellDev& S, bool fp32, const double* B, int64_t ldb, double* C,
+                        int64_t ldc, int k, cudaStream_t s);
+cudaError_t launch_halo(const HaloDev& H, bool fp32, const double* B, int64_t ldb, double* C,
+                        int64_t ldc, int k, cudaStream_t s);
+cudaError_t launch_zero_rows(double* C, int64_t n_rows, int64_t ldc, int k, cudaStream_t s);
+
+}  // namespace spmv

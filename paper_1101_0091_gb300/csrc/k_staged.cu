@@ -1,0 +1,168 @@
+// CRS_STAGED: thread-per-row CRS product with bulk-copied tiles (Sec. 1.2 loop).
+//
+// The row range of the matrix is cut into blocks (host side, build_row_blocks).
+// A "tile" block holds up to 256 consecutive rows of at most 64 entries whose
+// entries, being contiguous in val/col_idx, fit one shared-memory tile.  One
+// elected thread brings the block's val and col_idx slices into shared memory
+// with two one-dimensional bulk copies (cp.async.bulk, TMA engine) completing
+// on an mbarrier; meanwhile every thread reads its row bounds.  Then each thread
+// walks its own row from shared memory, gathers B with read-only loads, and
+// accumulates in FP64 with one FMA per entry.  On this GPU the FP64 pipe
+// sustains about two FMAs per SM clock, so the kernel does no shuffle
+// reductions at all for these rows.  A "warp" block holds up to 8 rows longer
+// than 64 entries, one warp per row: lanes stride the row with coalesced loads
+// and a 5-step xor-shuffle tree sums their partials.
+#include "device.cuh"
+
+namespace spmv {
+
+template <int K>
+struct Unroll {
+  static constexpr int value = K <= 2 ? 4 : (K <= 8 ? 2 : 1);
+};
+
+template <typename VT, int K>
+__device__ __forceinline__ void row_warp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, int row, const double* __restrict__ B,
+                                         int64_t ldb, double* __restrict__ C, int64_t ldc, int k,
+                                         int accumulate) {
+  const int lane = threadIdx.x & 31;
+  const int rs = __ldg(row_ptr + row), re = __ldg(row_ptr + row + 1);
+  double acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = 0.0;
+  for (int j = rs + lane; j < re; j += 32) {
+    const double v = to_f64(ldcs(val + j));
+    const double* b = B + (int64_t)ldcs(col + j) * ldb;
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = warp_sum_xor(acc[q], 32);
+  double* out = C + (int64_t)row * ldc;
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q < k && lane == q) out[q] = accumulate ? out[q] + acc[q] : acc[q];
+}
+
+template <typename VT, int K>
+__global__ void __launch_bounds__(kThreads)
+    k_crs_staged(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                 const VT* __restrict__ val, const uint32_t* __restrict__ blk, int tile,
+                 const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc, int k,
+                 int accumulate, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+
+  const uint32_t e0 = __ldg(blk + blockIdx.x), e1 = __ldg(blk + blockIdx.x + 1);
+  const int r0 = (int)(e0 & ~kBlockWarpFlag), r1 = (int)(e1 & ~kBlockWarpFlag);
+  const int tid = threadIdx.x;
+
+  if (e0 & kBlockWarpFlag) {  // block of long rows: one warp per row
+    const int row = r0 + (tid >> 5);
+    if (row < r1) row_warp<VT, K>(row_ptr, col, val, row, B, ldb, C, ldc, k, accumulate);
+    return;
+  }
+
+  const int bs = __ldg(row_ptr + r0), be = __ldg(row_ptr + r1);
+  constexpr int VA = 16 / (int)sizeof(VT);  // value entries per 16 bytes
+  const int v_lo = bs & ~(VA - 1), v_hi = (be + VA - 1) & ~(VA - 1);
+  const int c_lo = bs & ~3, c_hi = (be + 3) & ~3;
+  VT* sval = reinterpret_cast<VT*>(smem);
+  const int32_t* scol = reinterpret_cast<const int32_t*>(smem + sizeof(VT) * (size_t)(tile + 8));
+  const bool any = be > bs;
+
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (any && tid == 0) {
+    const uint32_t vb = (uint32_t)(v_hi - v_lo) * (uint32_t)sizeof(VT);
+    const uint32_t cb = (uint32_t)(c_hi - c_lo) * 4u;
+    mbar_arrive_expect_tx(&bar, vb + cb);
+    bulk_g2s(sval, val + v_lo, vb, &bar);
+    bulk_g2s(smem + sizeof(VT) * (size_t)(tile + 8), col + c_lo, cb, &bar);
+  }
+
+  const int row = r0 + tid;
+  int rs = 0, re = 0;
+  if (row < r1) {
+    rs = __ldg(row_ptr + row);
+    re = __ldg(row_ptr + row + 1);
+  }
+  if (any && !mbar_wait_bounded(&bar, 0, kWaitLimitNs)) {
+    atomicExch(status, DEV_WAIT_TIMEOUT);
+    mbar_wait_bounded(&bar, 0, kWaitLimitNs);  // let the copies in flight land before exiting
+    return;
+  }
+  if (row >= r1) return;
+
+  double acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = 0.0;
+  constexpr int U = Unroll<K>::value;
+  int j = rs;
+  for (; j + U <= re; j += U) {
+    double v[U];
+    const double* b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = to_f64(sval[j + u - v_lo]);
+      b[u] = B + (int64_t)scol[j + u - c_lo] * ldb;
+    }
+    double g[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) g[u][q] = (q < k) ? __ldg(b[u] + q) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
+  }
+  for (; j < re; ++j) {
+    const double v = to_f64(sval[j - v_lo]);
+    const double* b = B + (int64_t)scol[j - c_lo] * ldb;
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+  }
+  double* out = C + (int64_t)row * ldc;
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q < k) out[q] = accumulate ? out[q] + acc[q] : acc[q];
+}
+
+template <typename VT, int K>
+static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
+                                   int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
+  const size_t smem = sizeof(VT) * (size_t)(A.tile + 8) + 4 * (size_t)(A.tile + 8);
+  auto kern = k_crs_staged<VT, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)A.n_blk, kThreads, smem, s>>>(A.row_ptr, A.col, val, A.blk, A.tile, B, ldb, C, ldc, k,
+                                                  accumulate ? 1 : 0, status);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t dispatch_staged(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
+                                   int64_t ldc, int k, bool acc, int* status, cudaStream_t s) {
+  if (k <= 1) return launch_staged_t<VT, 1>(A, val, B, ldb, C, ldc, k, acc, status, s);
+  if (k <= 2) return launch_staged_t<VT, 2>(A, val, B, ldb, C, ldc, k, acc, status, s);
+  if (k <= 4) return launch_staged_t<VT, 4>(A, val, B, ldb, C, ldc, k, acc, status, s);
+  if (k <= 8) return launch_staged_t<VT, 8>(A, val, B, ldb, C, ldc, k, acc, status, s);
+  return launch_staged_t<VT, 16>(A, val, B, ldb, C, ldc, k, acc, status, s);
+}
+
+cudaError_t launch_crs_staged(const CsrDev& A, bool fp32, const double* B, int64_t ldb, double* C,
+                              int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
+  if (A.n_blk == 0) return cudaSuccess;
+  if (fp32) return dispatch_staged<float>(A, A.val32, B, ldb, C, ldc, k, accumulate, status, s);
+  return dispatch_staged<double>(A, A.val, B, ldb, C, ldc, k, accumulate, status, s);
+}
+
+}  // namespace spmv

@@ -1,0 +1,205 @@
+"""GPU parity of every CRS/SELL variant against the oracle (single vector and
+blocks of k right-hand sides, FP64 and FP32-stored values), edge cases and
+error paths, all through the C ABI."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_util import TOL_FP32VAL, TOL_FP64, assert_close, dev, host, run
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [("crs_staged", 1, 1), ("crs_l1", 2, 1), ("crs_l2", 3, 1), ("crs_l4", 4, 1), ("crs_l8", 5, 1),
+            ("crs_l16", 6, 1), ("crs_l32", 7, 1), ("sell_s1", 8, 1), ("sell_s256", 8, 256),
+            ("sell_s4096", 8, 4096)]
+VIDS = [v[0] for v in VARIANTS]
+
+_CASES = {}
+
+
+def case(name):
+    if name not in _CASES:
+        if name == "laplace256":          # the 2D 5-point workload at full size
+            _CASES[name] = gen.laplace2d(256)
+        elif name == "poisson40":         # 3D variable-coefficient stencil, 64,000 rows
+            _CASES[name] = gen.poisson3d_var(40)
+        elif name == "eigen":             # eigenproblem-shaped, many tiles
+            _CASES[name] = gen.eigen_shaped(150_000, window=1 << 16)
+        elif name == "powerlaw":          # rows up to 2000 long (warp-per-row blocks)
+            _CASES[name] = gen.powerlaw(30_000, seed=1)
+        elif name == "ragged":            # unsorted, duplicates, empty rows, odd sizes
+            _CASES[name] = gen.random_csr(1037, 911, 0.012, 5, empty_rows=0.2, duplicates=True, unsorted=True)
+        elif name == "integer":
+            _CASES[name] = gen.random_csr(3001, 2999, 0.004, 6, integer=True, empty_rows=0.05, duplicates=True)
+    return _CASES[name]
+
+
+def make(lib, A, vid, sigma, **kw):
+    return lib.Plan.from_csr(A, variant=vid, sell_sigma=sigma, **kw)
+
+
+@pytest.mark.parametrize("name", ["laplace256", "poisson40", "eigen", "powerlaw", "ragged"])
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_spmv_matches_oracle(lib, name, variant):
+    A = case(name)
+    B = gen.uniform(A.n_cols, seed=7)
+    with make(lib, A, variant[1], variant[2]) as p:
+        assert p.info().variant == variant[1]
+        assert_close(run(p, B), A, B)
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_integer_bit_exact(lib, variant):
+    """Integer values |v| <= 2^10 and short rows: every partial sum is exact, so
+    any summation order gives the oracle's result bit for bit."""
+    A = case("integer")
+    B = np.random.default_rng(0).integers(-1024, 1025, A.n_cols).astype(np.float64)
+    with make(lib, A, variant[1], variant[2]) as p:
+        assert_close(run(p, B), A, B, exact=True)
+        Bk = np.random.default_rng(1).integers(-1024, 1025, (A.n_cols, 4)).astype(np.float64)
+        assert_close(run(p, Bk), A, Bk, exact=True)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 13, 16])
+@pytest.mark.parametrize("variant", [VARIANTS[0], VARIANTS[1], VARIANTS[4], VARIANTS[6], VARIANTS[8]],
+                         ids=["crs_staged", "crs_l1", "crs_l8", "crs_l32", "sell_s256"])
+def test_spmm_block(lib, k, variant):
+    for name in ("laplace256", "powerlaw"):
+        A = case(name)
+        B = gen.rhs_block(A.n_cols, k, seed=k)
+        with make(lib, A, variant[1], variant[2]) as p:
+            assert_close(run(p, B), A, B)
+
+
+def test_spmm_leading_dimensions(lib):
+    """ldb > k and ldc > k: only the first k columns are read and written."""
+    import torch
+    A = case("eigen")
+    k = 3
+    B = gen.rhs_block(A.n_cols, 8, seed=3)
+    with lib.Plan.from_csr(A) as p:
+        Bd = dev(B)
+        C = torch.full((A.n_rows, 6), 7.0, dtype=torch.float64, device="cuda")
+        p.apply_block(Bd, C, k)
+        y = host(C)
+        assert np.all(y[:, k:] == 7.0)
+        assert_close(np.ascontiguousarray(y[:, :k]), A, np.ascontiguousarray(B[:, :k]))
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_fp32_values(lib, variant):
+    """FP32-stored values: equal (to FP64 rounding) to the oracle's loop over
+    float-rounded values, and within 2e-7 * sum|ab| of the FP64 product."""
+    A = case("eigen")
+    B = gen.uniform(A.n_cols, seed=9)
+    Bk = gen.rhs_block(A.n_cols, 4, seed=10)
+    with make(lib, A, variant[1], variant[2], val_fp32=True) as p:
+        assert p.info().val_fp32 == 1
+        y = run(p, B)
+        assert_close(y, A, B, tol=TOL_FP64, f32val=True)
+        assert_close(y, A, B, tol=TOL_FP32VAL)
+        yk = run(p, Bk)
+        assert_close(yk, A, Bk, tol=TOL_FP64, f32val=True)
+        assert_close(yk, A, Bk, tol=TOL_FP32VAL)
+
+
+@pytest.mark.parametrize("variant", [VARIANTS[0], VARIANTS[1], VARIANTS[7]], ids=["crs_staged", "crs_l1", "sell"])
+def test_fp32_widening_special_values(lib, variant):
+    """The integer-pipe float->double widening is exact for zeros of both signs,
+    normals across the exponent range, and subnormal floats."""
+    vals = np.array([0.0, -0.0, 1.0, -1.0, 3.1415926535, 1e-30, -2.5e30, 3.4e38, 1.2e-38, 1e-40, -7e-45,
+                     1.17549435e-38, 6.0e-39, 123456.789, -0.1], dtype=np.float64)
+    n = len(vals)
+    A = gen.CSR(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), vals)
+    B = np.ones(n)
+    with make(lib, A, variant[1], variant[2], val_fp32=True) as p:
+        y = run(p, B)
+    ref = vals.astype(np.float32).astype(np.float64) + 0.0   # 0.0 + x turns -0 into +0, as the loop does
+    assert np.array_equal(y, ref)
+    assert np.array_equal(np.signbit(y), np.signbit(ref))
+
+
+def test_edge_cases(lib):
+    # no rows at all
+    A = gen.CSR(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    with lib.Plan.from_csr(A) as p:
+        p.apply(dev(np.ones(5)), dev(np.zeros(1)))
+        p.check()
+    # only empty rows: C is overwritten with +0.0 by every variant
+    A = gen.CSR(700, 5, np.zeros(701, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    for _, vid, sig in VARIANTS:
+        with make(lib, A, vid, sig) as p:
+            y = run(p, np.ones(5))
+            assert np.array_equal(y, np.zeros(700)) and not np.signbit(y).any()
+    # 1 x 1
+    A = gen.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    for _, vid, sig in VARIANTS:
+        with make(lib, A, vid, sig) as p:
+            assert run(p, np.array([-2.5]))[0] == -7.5
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_row_length_boundaries(lib, variant):
+    """Rows of length 63/64/65 (the warp-row threshold), longer than a tile,
+    mixed with empty and short rows, with an odd nnz and an odd row count."""
+    lens = [0, 1, 63, 64, 65, 2, 0, 7, 600, 5000, 12000, 3, 1, 0, 9999] + [5] * 513 + [1]
+    A = gen.csr_from_lengths(lens, 20000, seed=11)
+    assert A.nnz % 2 == 1
+    B = gen.uniform(A.n_cols, seed=12)
+    with make(lib, A, variant[1], variant[2]) as p:
+        assert_close(run(p, B), A, B)
+        Bk = gen.rhs_block(A.n_cols, 4, seed=13)
+        assert_close(run(p, Bk), A, Bk)
+
+
+def test_deterministic(lib):
+    A = case("powerlaw")
+    B = gen.uniform(A.n_cols, seed=1)
+    for _, vid, sig in VARIANTS:
+        with make(lib, A, vid, sig) as p:
+            assert np.array_equal(run(p, B), run(p, B))
+
+
+def test_apply_host_end_to_end(lib):
+    A = case("eigen")
+    B = gen.uniform(A.n_cols, seed=2)
+    Bk = gen.rhs_block(A.n_cols, 4, seed=3)
+    with lib.Plan.from_csr(A) as p:
+        assert np.array_equal(p.apply_host(B), run(p, B))
+        assert np.array_equal(p.apply_host(Bk, k=4), run(p, Bk))
+
+
+def test_set_variant_switches(lib):
+    A = case("poisson40")
+    B = gen.uniform(A.n_cols, seed=4)
+    with lib.Plan.from_csr(A) as p:
+        assert p.info().variant == lib.SPMV_CRS_STAGED
+        for _, vid, sig in VARIANTS:
+            p.set_variant(vid, sig)
+            assert p.info().variant == vid
+            assert_close(run(p, B), A, B)
+
+
+def test_error_paths(lib):
+    A = case("ragged")
+    with lib.Plan.from_csr(A, max_k=4) as p:
+        B = dev(np.ones(A.n_cols))
+        C = dev(np.zeros(A.n_rows))
+        for bad_k in (0, 5, 17):
+            with pytest.raises(lib.SpmvError) as e:
+                lib.spmv_apply_block(p.handle, B.data_ptr(), bad_k, bad_k + 1, C.data_ptr(), bad_k + 1, 0)
+            assert e.value.status == 1
+        with pytest.raises(lib.SpmvError) as e:
+            lib.spmv_apply_block(p.handle, B.data_ptr(), 2, 1, C.data_ptr(), 2, 0)
+        assert e.value.status == 1
+        with pytest.raises(lib.SpmvError) as e:
+            p.apply_split(B, B, C)
+        assert e.value.status == 6
+        with pytest.raises(lib.SpmvError) as e:
+            p.set_variant(99)
+        assert e.value.status == 1
+        with pytest.raises(lib.SpmvError) as e:
+            p.sell_export()
+        assert e.value.status == 6
+        p.check()

@@ -1,0 +1,99 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times, on sampled rows the oracle computes one by one (the oracle runs the
+same row loop on the sampled rows only)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_util import TOL_FP32VAL, TOL_FP64, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def sample_rows(n, seed, count=30_000, edge=500):
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([np.arange(min(edge, n)), np.arange(max(0, n - edge), n), rng.integers(0, n, count)])
+    return np.unique(rows)
+
+
+def sub_csr(A, rows):
+    lens = (A.row_ptr[rows + 1] - A.row_ptr[rows]).astype(np.int64)
+    rp = np.zeros(len(rows) + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    idx = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1]) for r in rows]) if len(rows) else np.zeros(0, int)
+    return gen.CSR(len(rows), A.n_cols, rp.astype(np.int32), A.col_idx[idx], A.val[idx])
+
+
+def check_sampled(y, A, B, rows, tol=TOL_FP64, f32val=False):
+    S = sub_csr(A, rows)
+    if f32val:
+        ref = oracle.spmm(S, B.reshape(-1, 1), f32val=True)[:, 0]
+    else:
+        ref = oracle.spmv(S, B)
+    r = oracle.max_err_ratio(y[rows], ref, oracle.abs_scale(S, B), tol)
+    assert r <= 1.0, r
+    return r
+
+
+@pytest.fixture(scope="module")
+def poisson280():
+    return gen.poisson3d_var(280)
+
+
+def test_poisson280_staged_and_split(lib, poisson280):
+    import torch
+    A = poisson280
+    assert (A.n_rows, A.nnz) == (21_952_000, 153_193_600)
+    B = gen.uniform(A.n_cols, seed=0)
+    h = A.n_cols - A.n_cols // 10
+    rows = sample_rows(A.n_rows, 1)
+    with lib.Plan.from_csr(A, halo_begin=h) as p:
+        Bd = dev(B)
+        C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply(Bd, C)
+        p.check()
+        y = host(C)
+        assert not np.isnan(y).any()
+        check_sampled(y, A, B, rows)
+        # split product with the halo copied from pinned host memory on a side stream
+        halo = torch.from_numpy(B[h:].copy()).pin_memory()
+        Bd[h:] = float("nan")
+        C.fill_(float("nan"))
+        p.apply_split(Bd, halo, C, torch.cuda.current_stream(), torch.cuda.Stream())
+        p.check()
+        y2 = host(C)
+        assert not np.isnan(y2).any()
+        check_sampled(y2, A, B, rows)
+
+
+def test_poisson280_fp32_values(lib, poisson280):
+    import torch
+    A = poisson280
+    B = gen.uniform(A.n_cols, seed=0)
+    rows = sample_rows(A.n_rows, 2, count=10_000)
+    with lib.Plan.from_csr(A, val_fp32=True) as p:
+        C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        p.apply(dev(B), C)
+        p.check()
+        y = host(C)
+    check_sampled(y, A, B, rows, f32val=True)
+    check_sampled(y, A, B, rows, tol=TOL_FP32VAL)
+
+
+def test_eigen_full_staged_and_sell(lib):
+    import torch
+    A = gen.eigen_shaped()
+    assert A.n_rows == 6_201_600
+    B = gen.uniform(A.n_cols, seed=0)
+    rows = sample_rows(A.n_rows, 3)
+    with lib.Plan.from_csr(A) as p:
+        Bd = dev(B)
+        C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        for vid, sigma in [(lib.SPMV_CRS_STAGED, 1), (lib.SPMV_SELL, 1), (lib.SPMV_SELL, 256),
+                           (lib.SPMV_SELL, 4096), (lib.SPMV_CRS_L4, 1)]:
+            p.set_variant(vid, sigma)
+            C.fill_(float("nan"))
+            p.apply(Bd, C)
+            p.check()
+            check_sampled(host(C), A, B, rows)
