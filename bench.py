@@ -4,8 +4,9 @@
 Workload (default): the 3D 7-point variable-coefficient Poisson stencil on a
 280^3 grid (N = 21,952,000 rows, 153,193,600 nonzeros, FP64 CRS), the stand-in
 for the paper's sAMG matrix.  One step = one product C = A*B with the plan's
-default kernel (CRS_STAGED).  Inputs (2.28 GB) exceed L2 (129 MB), so no flush
-is needed between steps.
+default kernel (CRS_L1: thread per row, val/col slices of the CTA 152 positions
+ahead prefetched into L2 by the TMA engine).  Inputs (2.28 GB) exceed L2
+(129 MB), so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
 Under torchrun each rank runs an independent replica (the path does not shard
@@ -30,7 +31,11 @@ sys.path.insert(0, ROOT)
 METRIC = "spMVM GFlop/s & HBM GB/s vs roofline; chosen form vs plain CRS at stated err"
 WORKLOADS = {
     "poisson3d_280": "3D 7-point variable-coefficient Poisson stencil, 280^3 grid, N=21,952,000, nnz=153,193,600, FP64 CRS, B~U[-1,1) seed 0",
+    "poisson3d_160": "3D 7-point variable-coefficient Poisson stencil, 160^3 grid, N=4,096,000, nnz=28,518,400, FP64 CRS (profiling size)",
+    "eigen_6201600": "symmetric eigenproblem-shaped matrix, N=6,201,600 (400 x 15,504), ~13.8 nnz/row, FP64 CRS",
 }
+VARIANTS = {"crs_staged": (1, 1), "crs_l1": (2, 1), "crs_l2": (3, 1), "crs_l4": (4, 1), "crs_l8": (5, 1),
+            "crs_l16": (6, 1), "crs_l32": (7, 1), "sell_s1": (8, 1), "sell_s256": (8, 256), "sell_s4096": (8, 4096)}
 
 
 def parse():
@@ -40,8 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson3d_280", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-forms", action="store_true", help="skip the per-form comparison lines")
+    ap.add_argument("--variant", default="crs_l1", choices=sorted(VARIANTS))
+    ap.add_argument("--fp32-val", action="store_true", help="store val in FP32 (FP64 accumulation)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     return ap.parse_args()
 
 
@@ -51,11 +58,13 @@ def dist_info():
 
 def load_workload(name):
     import gen
-    if name == "poisson3d_280":
-        A = gen.poisson3d_var(280, seed=0)
-        B = gen.uniform(A.n_cols, seed=0)
-        return A, B
-    raise ValueError(name)
+    if name.startswith("poisson3d_"):
+        A = gen.poisson3d_var(int(name.split("_")[1]), seed=0)
+    elif name == "eigen_6201600":
+        A = gen.eigen_shaped(6_201_600, seed=0)
+    else:
+        raise ValueError(name)
+    return A, gen.uniform(A.n_cols, seed=0)
 
 
 def measured_peaks():
@@ -196,12 +205,12 @@ def main():
         torch.cuda.set_device(0)
     spmv.load()
     A, Bh = load_workload(args.workload)
-    plan = spmv.Plan.from_csr(A)
-    info = plan.info()
+    vid, sigma = VARIANTS[args.variant]
+    plan = spmv.Plan.from_csr(A, variant=vid, sell_sigma=sigma, val_fp32=args.fp32_val)
     stream = torch.cuda.Stream()
     B = torch.from_numpy(Bh).cuda()
     C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
-    traffic = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz)
+    traffic = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4 if args.fp32_val else 8)
     hbm_peak, peak_kind = measured_peaks()
 
     def barrier():
@@ -239,35 +248,39 @@ def main():
     achieved = traffic.bytes_min / kern_s / 1e9
 
     # end to end through the C ABI from pinned host buffers (H2D of B, D2H of C inside the timed region)
-    Bpin = torch.from_numpy(Bh).pin_memory()
-    Cpin = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
-    e2e_steps = max(3, min(args.steps, 20))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
-    e2e_t = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_t], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e = None
+    if not args.no_e2e:
+        Bpin = torch.from_numpy(Bh).pin_memory()
+        Cpin = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
+        e2e_steps = max(3, min(args.steps, 20))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
+        e2e_t = (time.perf_counter() - t0) / e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_t], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        e2e = {"value": round(flops_all / e2e_t / 1e9, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 8 * A.n_cols,
+               "d2h_bytes_per_step": 8 * A.n_rows}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": "crs_staged",
-                   "n_rows": A.n_rows, "nnz": A.nnz, "l2": "inputs larger than L2 (2.28 GB vs 129 MB), no flush",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": args.variant,
+                   "val_storage": "f32" if args.fp32_val else "f64", "n_rows": A.n_rows, "nnz": A.nnz,
+                   "l2": f"inputs larger than L2 ({traffic.bytes_min / 1e9:.2f} GB vs 129 MB), no flush",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "hbm_gbs": round(achieved, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
-                     "traffic": ncu_traffic("crs_staged", args.workload),
+                     "traffic": ncu_traffic(args.variant, args.workload),
                      "algorithmic_bytes_per_launch": traffic.bytes_min},
-        "e2e": {"value": round(flops_all / e2e_t / 1e9, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 8 * A.n_cols,
-                "d2h_bytes_per_step": 8 * A.n_rows},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 4),

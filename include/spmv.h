@@ -55,7 +55,7 @@ typedef enum {
 /* Kernel variants.  All compute the same product with FP64 accumulation and
  * one fused multiply-add per stored entry. */
 typedef enum {
-  SPMV_VARIANT_AUTO = 0,   /* the plan's choice (cost model if attached, else CRS_STAGED)       */
+  SPMV_VARIANT_AUTO = 0,   /* the plan's default: CRS_L1 (a tuner or the cost model may switch)  */
   SPMV_CRS_STAGED = 1,     /* thread per row; each CTA's contiguous val/col tile is brought     */
                            /* into shared memory by one bulk copy (cp.async.bulk + mbarrier);   */
                            /* rows longer than 64 go to warp-per-row blocks                      */
@@ -144,6 +144,18 @@ spmv_status spmv_apply_host(spmv_handle h, const double* B_host, int32_t k, doub
 spmv_status spmv_set_variant(spmv_handle h, int32_t variant, int32_t sell_sigma);
 
 spmv_status spmv_get_info(spmv_handle h, spmv_info* info);
+
+/* Launch parameters a tuner may change without touching the result.
+ * prefetch_distance: each CTA of the row and SELL kernels asks the TMA engine
+ * to prefetch into L2 the matrix slice of the CTA this many positions ahead
+ * (cp.async.bulk.prefetch.L2); 0 disables it. */
+typedef struct {
+  int32_t prefetch_distance;
+  int32_t reserved[7];
+} spmv_tuning;
+
+spmv_status spmv_set_tuning(spmv_handle h, const spmv_tuning* t);
+spmv_status spmv_get_tuning(spmv_handle h, spmv_tuning* t);
 
 /* Wait for the plan's work on `stream`, then read and clear the plan's device
  * status word: SPMV_ERR_DEVICE (message names the failing step) if a kernel

@@ -17,7 +17,8 @@ from . import _binding as _b
 from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_block, spmv_apply_host,  # noqa: F401
                        spmv_apply_split, spmv_check, spmv_create, spmv_default_options, spmv_destroy,
                        spmv_get_info, spmv_last_error, spmv_options, spmv_sell_export, spmv_set_variant,
-                       spmv_split_export, spmv_features, SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
+                       spmv_split_export, spmv_features, spmv_set_tuning, spmv_get_tuning, spmv_tuning,
+                       SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
                        SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_N_VARIANTS)
 
 LANE_VARIANTS = {1: SPMV_CRS_L1, 2: SPMV_CRS_L2, 4: SPMV_CRS_L4, 8: SPMV_CRS_L8, 16: SPMV_CRS_L16,
@@ -94,6 +95,15 @@ class Plan:
 
     def info(self):
         return spmv_get_info(self.handle)
+
+    def set_tuning(self, prefetch_distance: int | None = None) -> None:
+        t = spmv_get_tuning(self.handle)
+        if prefetch_distance is not None:
+            t.prefetch_distance = prefetch_distance
+        spmv_set_tuning(self.handle, t)
+
+    def tuning(self):
+        return spmv_get_tuning(self.handle)
 
     def check(self, stream=None) -> None:
         spmv_check(self.handle, _stream_handle(stream))

@@ -154,3 +154,21 @@ def spmv_split_export(h, loc_row_ptr, loc_col, loc_val, halo_rows, halo_row_ptr,
 
 def spmv_features(n_rows: int, n_cols: int, row_ptr: int, col_idx: int, k: int, out: int) -> None:
     _check(load().spmv_features(n_rows, n_cols, row_ptr, col_idx, k, out))
+
+
+class spmv_tuning(ctypes.Structure):
+    _fields_ = [("prefetch_distance", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_SIGS["spmv_set_tuning"] = ([_vp, ctypes.POINTER(spmv_tuning)], ctypes.c_int)
+_SIGS["spmv_get_tuning"] = ([_vp, ctypes.POINTER(spmv_tuning)], ctypes.c_int)
+
+
+def spmv_set_tuning(h, t: spmv_tuning) -> None:
+    _check(load().spmv_set_tuning(h, ctypes.byref(t)))
+
+
+def spmv_get_tuning(h) -> spmv_tuning:
+    t = spmv_tuning()
+    _check(load().spmv_get_tuning(h, ctypes.byref(t)))
+    return t

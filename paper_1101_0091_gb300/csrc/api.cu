@@ -107,7 +107,14 @@ struct spmv_plan {
   double* d_B = nullptr;
   double* d_C = nullptr;
   int64_t scratch_k = 0;
+  spmv_tuning tuning{};
 };
+
+static void apply_tuning(spmv_plan* p) {
+  p->A.prefetch = p->tuning.prefetch_distance;
+  p->local.prefetch = p->tuning.prefetch_distance;
+  p->sell.prefetch = p->tuning.prefetch_distance;
+}
 
 static spmv_status build_blocks(spmv_plan* p, CsrDev* M, const int32_t* host_row_ptr) {
   int tile = 0;
@@ -150,12 +157,14 @@ static spmv_status build_sell_dev(spmv_plan* p, int sigma) {
   p->sell.chunk_len = clen;
   p->sell.col = col;
   p->sell.val = val;
+  p->sell.prefetch = p->tuning.prefetch_distance;
   if (p->opt.val_fp32) {
     std::vector<float> v32(S.val.begin(), S.val.end());
     float* d32;
     SPMV_CUDA(upload(p->arena, &d32, v32.data(), S.slots, 4));
     p->sell_ptrs.push_back(d32);
     p->sell.val32 = d32;
+    p->sell.val32_special = has_special_f32(v32.data(), S.slots);
   }
   std::vector<double>().swap(p->sell_host.val);  // values live on the device; keep the index arrays
   return SPMV_OK;
@@ -179,6 +188,7 @@ static spmv_status upload_csr(spmv_plan* p, CsrDev* M, int64_t n_rows, int64_t n
     float* d32;
     SPMV_CUDA(upload(p->arena, &d32, v32.data(), nnz, pad_to(nnz, 4)));
     M->val32 = d32;
+    M->val32_special = has_special_f32(v32.data(), nnz);
   }
   return SPMV_OK;
 }
@@ -204,6 +214,7 @@ static spmv_status build_split_dev(spmv_plan* p, int64_t h) {
   p->halo.col = hc.col;
   p->halo.val = hc.val;
   p->halo.val32 = hc.val32;
+  p->halo.val32_special = hc.val32_special;
   SPMV_CUDA(cudaEventCreateWithFlags(&p->ev_main, cudaEventDisableTiming));
   SPMV_CUDA(cudaEventCreateWithFlags(&p->ev_copy, cudaEventDisableTiming));
   p->has_split = true;
@@ -211,7 +222,7 @@ static spmv_status build_split_dev(spmv_plan* p, int64_t h) {
 }
 
 static spmv_status prepare_variant(spmv_plan* p, int variant, int sigma) {
-  if (variant == SPMV_VARIANT_AUTO) variant = SPMV_CRS_STAGED;
+  if (variant == SPMV_VARIANT_AUTO) variant = SPMV_CRS_L1;
   if (variant < SPMV_CRS_STAGED || variant >= SPMV_N_VARIANTS)
     return fail(SPMV_ERR_ARG, "unknown variant " + std::to_string(variant));
   if (variant == SPMV_CRS_STAGED && !p->blocks_built) {
@@ -283,6 +294,7 @@ spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, const 
     return fail(SPMV_ERR_OOM, "host allocation failed");
   }
   p->opt = o;
+  p->tuning.prefetch_distance = kDefaultPrefetch;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   auto cleanup = [&](spmv_status st) {
@@ -304,6 +316,7 @@ spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, const 
   }
   st = prepare_variant(p.get(), o.variant, o.sell_sigma);
   if (st != SPMV_OK) return cleanup(st);
+  apply_tuning(p.get());
   *out = p.release();
   return SPMV_OK;
 }
@@ -396,6 +409,20 @@ spmv_status spmv_set_variant(spmv_handle h, int32_t variant, int32_t sell_sigma)
   if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
   DeviceGuard g(h->device);
   return prepare_variant(h, variant, sell_sigma);
+}
+
+spmv_status spmv_set_tuning(spmv_handle h, const spmv_tuning* t) {
+  if (!h || !t) return fail(SPMV_ERR_ARG, "NULL argument");
+  if (t->prefetch_distance < 0) return fail(SPMV_ERR_ARG, "prefetch_distance must be >= 0");
+  h->tuning = *t;
+  apply_tuning(h);
+  return SPMV_OK;
+}
+
+spmv_status spmv_get_tuning(spmv_handle h, spmv_tuning* t) {
+  if (!h || !t) return fail(SPMV_ERR_ARG, "NULL argument");
+  *t = h->tuning;
+  return SPMV_OK;
 }
 
 spmv_status spmv_get_info(spmv_handle h, spmv_info* info) {

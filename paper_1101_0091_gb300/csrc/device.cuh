@@ -67,38 +67,49 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Exact binary32 -> binary64 widening from the IEEE 754 formats, done in the
-// integer pipe: for a normal float the exponent is rebiased by 1023 - 127 = 896
-// and the 23-bit fraction moves to the top of the 52-bit fraction.  Zeros keep
-// their sign.  Subnormal, infinite and NaN inputs (never produced by rounding
-// finite matrix values of normal range) take the hardware conversion.  On this
-// GPU the hardware f32->f64 conversion shares the FP64 pipe with the FMAs, so
-// the common path avoids it.
-__device__ __forceinline__ double widen_f32(float f) {
+// FP32-stored values come in two storage types with the same layout:
+//  - f32n: every value is zero or a normal float (the plan checks this on the
+//    host when it rounds the values).  Widened exactly in the integer pipe from
+//    the IEEE 754 formats: with sign s, biased exponent e and 23-bit fraction m,
+//    a normal float is 2^(e-127) * 1.m, the same number as the double with
+//    exponent e + (1023 - 127) and fraction m << 29; zero keeps its sign.
+//    On this GPU the hardware f32->f64 conversion issues on the FP64 pipe that
+//    the FMAs already saturate, so this path avoids it.
+//  - float: values that include subnormal, infinite or NaN floats; widened by
+//    the hardware conversion (exact for every input).
+struct f32n {
+  float v;
+};
+
+__device__ __forceinline__ double widen_f32n(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t a = u & 0x7fffffffu;
-  uint32_t hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
-  uint32_t lo = u << 29;
-  if (a == 0) {
-    hi = u & 0x80000000u;
-    lo = 0;
-  } else if (a - 0x00800000u >= 0x7f000000u) {
-    return (double)f;
-  }
+  const uint32_t hi = a ? ((u & 0x80000000u) | ((a >> 3) + (896u << 20))) : (u & 0x80000000u);
+  const uint32_t lo = a ? (u << 29) : 0u;
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Fire-and-forget bulk prefetch of [p, p + bytes) into L2 (TMA engine).  p and
+// bytes must be multiples of 16 and the range inside the allocation.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  if (bytes == 0) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ double to_f64(double v) { return v; }
-__device__ __forceinline__ double to_f64(float v) { return widen_f32(v); }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(f32n v) { return widen_f32n(v.v); }
 
 // Read-only loads through the non-coherent path.
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ldg(const float* p) { return __ldg(p); }
+__device__ __forceinline__ f32n ldg(const f32n* p) { return f32n{__ldg(reinterpret_cast<const float*>(p))}; }
 __device__ __forceinline__ int32_t ldg(const int32_t* p) { return __ldg(p); }
 
 // Streaming loads (evict-first): matrix entries are used once per product.
 __device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ldcs(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ f32n ldcs(const f32n* p) { return f32n{__ldcs(reinterpret_cast<const float*>(p))}; }
 __device__ __forceinline__ int32_t ldcs(const int32_t* p) { return __ldcs(p); }
 
 __device__ __forceinline__ double warp_sum_xor(double x, int width) {

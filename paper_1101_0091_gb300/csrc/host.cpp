@@ -47,6 +47,16 @@ bool validate_csr(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const 
   return true;
 }
 
+bool has_special_f32(const float* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t u;
+    std::memcpy(&u, v + i, 4);
+    const uint32_t a = u & 0x7fffffffu;
+    if (a != 0 && (a < 0x00800000u || a >= 0x7f800000u)) return true;
+  }
+  return false;
+}
+
 // Blocks of CRS_STAGED.  A tile block: consecutive rows of length <= long_row,
 // at most rows_per_block rows and at most `tile` entries.  A warp block: up to
 // 8 consecutive rows longer than long_row.  Entry b is the first row of block b

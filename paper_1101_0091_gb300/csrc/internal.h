@@ -35,6 +35,7 @@ constexpr int kLongRow = 64;         // rows longer than this are handled warp-p
 constexpr int kWarpRowsPerBlock = kThreads / 32;
 constexpr int kSellC = 32;           // SELL chunk height
 constexpr uint32_t kBlockWarpFlag = 0x80000000u;  // high bit of a row-block entry: warp-per-row block
+constexpr int kDefaultPrefetch = 152;  // default L2 prefetch distance (CTAs ahead; one per SM)
 
 // ------------------------------------------------------- device buffers
 struct DevBuf {
@@ -71,7 +72,12 @@ struct CsrDev {
   const uint32_t* blk = nullptr;    // row blocks of CRS_STAGED (n_blk + 1 entries)
   int64_t n_blk = 0;
   int tile = 0;                     // nonzero capacity of a CRS_STAGED tile
+  int prefetch = 0;                 // CTAs ahead whose val/col slices are prefetched into L2 (0 = off)
+  bool val32_special = false;       // val32 holds a subnormal, infinite or NaN float
 };
+
+// True if any float is subnormal, infinite or NaN (zero and normals are "plain").
+bool has_special_f32(const float* v, int64_t n);
 
 struct SellDev {
   int64_t n_rows = 0, n_chunks = 0, slots = 0;
@@ -82,6 +88,8 @@ struct SellDev {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   const float* val32 = nullptr;
+  int prefetch = 0;                 // CTAs ahead whose slots are prefetched into L2 (0 = off)
+  bool val32_special = false;
 };
 
 // Halo part of a split: rows listed in `rows`, CRS over them.
@@ -92,6 +100,7 @@ struct HaloDev {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   const float* val32 = nullptr;
+  bool val32_special = false;
 };
 
 // ------------------------------------------------------- host builders

@@ -11,10 +11,26 @@
 namespace spmv {
 
 template <typename VT, int L, int K>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (K == 1 ? 8 : 1))
     k_crs_lanes(int64_t n_rows, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
                 const int32_t* __restrict__ col, const VT* __restrict__ val, const double* __restrict__ B,
-                int64_t ldb, double* __restrict__ C, int64_t ldc, int k, int accumulate) {
+                int64_t ldb, double* __restrict__ C, int64_t ldc, int k, int accumulate, int prefetch) {
+  constexpr int RPC = kThreads / L;  // rows per CTA
+  if (threadIdx.x == 0 && prefetch > 0) {
+    // bring the val/col slices of the CTA `prefetch` positions ahead into L2
+    const int64_t f0 = ((int64_t)blockIdx.x + prefetch) * RPC;
+    if (f0 < n_rows) {
+      const int64_t f1 = f0 + RPC < n_rows ? f0 + RPC : n_rows;
+      const int bs = __ldg(row_ptr + f0), be = __ldg(row_ptr + f1);
+      constexpr int VA = 16 / (int)sizeof(VT);
+      const int v_lo = bs & ~(VA - 1), v_hi = (be + VA - 1) & ~(VA - 1);
+      const int c_lo = bs & ~3, c_hi = (be + 3) & ~3;
+      if (be > bs) {
+        prefetch_l2(val + v_lo, (uint32_t)(v_hi - v_lo) * (uint32_t)sizeof(VT));
+        prefetch_l2(col + c_lo, (uint32_t)(c_hi - c_lo) * 4u);
+      }
+    }
+  }
   const int64_t g = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
   const int t = threadIdx.x % L;
   const bool active = g < n_rows;
@@ -26,30 +42,28 @@ __global__ void __launch_bounds__(kThreads)
   double acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0;
-  int j = rs + t;
-  if (L == 1) {
-    // two entries per step so that two gathers are in flight
-    for (; j + 1 < re; j += 2) {
-      const double v0 = to_f64(ldg(val + j)), v1 = to_f64(ldg(val + j + 1));
-      const double* b0 = B + (int64_t)ldg(col + j) * ldb;
-      const double* b1 = B + (int64_t)ldg(col + j + 1) * ldb;
-      double g0[K], g1[K];
+  // batches of NB entries per lane: all gathers of a batch are issued before its FMAs
+  constexpr int NB1 = sizeof(VT) == 8 ? 8 : 4;  // single-lane batch (FP32 storage: widening needs registers)
+  constexpr int NB = K >= 8 ? 1 : (L >= 4 ? 1 : (L == 2 ? (K >= 4 ? 1 : 4 / K) : NB1 / K > 0 ? NB1 / K : 1));
+  for (int j = rs + t; j < re; j += NB * L) {
+    double v[NB];
+    const double* b[NB];
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        g0[q] = (q < k) ? __ldg(b0 + q) : 0.0;
-        g1[q] = (q < k) ? __ldg(b1 + q) : 0.0;
-      }
+    for (int u = 0; u < NB; ++u) {
+      const int jj = (j + u * L < re) ? j + u * L : j;
+      v[u] = to_f64(L >= 8 ? ldcs(val + jj) : ldg(val + jj));
+      b[u] = B + (int64_t)(L >= 8 ? ldcs(col + jj) : ldg(col + jj)) * ldb;
+    }
+    double gv[NB][K];
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) gv[u][q] = (j + u * L < re && q < k) ? __ldg(b[u] + q) : 0.0;
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
 #pragma unroll
       for (int q = 0; q < K; ++q)
-        if (q < k) acc[q] = fma(v1, g1[q], fma(v0, g0[q], acc[q]));
-    }
-  }
-  for (; j < re; j += L) {
-    const double v = to_f64(L >= 8 ? ldcs(val + j) : ldg(val + j));
-    const double* b = B + (int64_t)(L >= 8 ? ldcs(col + j) : ldg(col + j)) * ldb;
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+        if (j + u * L < re && q < k) acc[q] = fma(v[u], gv[u][q], acc[q]);
   }
   if (L > 1) {
 #pragma unroll
@@ -67,53 +81,61 @@ __global__ void __launch_bounds__(kThreads)
 template <typename VT, int L, int K>
 static cudaError_t launch_lanes_t(int64_t n_rows, const int32_t* rows, const int32_t* row_ptr,
                                   const int32_t* col, const VT* val, const double* B, int64_t ldb, double* C,
-                                  int64_t ldc, int k, bool acc, cudaStream_t s) {
+                                  int64_t ldc, int k, bool acc, int pf, cudaStream_t s) {
   if (n_rows == 0) return cudaSuccess;
   const int64_t rows_per_cta = kThreads / L;
   const int64_t grid = (n_rows + rows_per_cta - 1) / rows_per_cta;
   k_crs_lanes<VT, L, K><<<(unsigned)grid, kThreads, 0, s>>>(n_rows, rows, row_ptr, col, val, B, ldb, C, ldc, k,
-                                                            acc ? 1 : 0);
+                                                            acc ? 1 : 0, pf);
   return cudaGetLastError();
 }
 
 template <typename VT, int L>
 static cudaError_t lanes_k(int64_t n, const int32_t* rows, const int32_t* rp, const int32_t* col, const VT* val,
                            const double* B, int64_t ldb, double* C, int64_t ldc, int k, bool acc,
-                           cudaStream_t s) {
-  if (k <= 1) return launch_lanes_t<VT, L, 1>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-  if (k <= 2) return launch_lanes_t<VT, L, 2>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-  if (k <= 4) return launch_lanes_t<VT, L, 4>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-  if (k <= 8) return launch_lanes_t<VT, L, 8>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-  return launch_lanes_t<VT, L, 16>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
+                           int pf, cudaStream_t s) {
+  if (k <= 1) return launch_lanes_t<VT, L, 1>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+  if (k <= 2) return launch_lanes_t<VT, L, 2>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+  if (k <= 4) return launch_lanes_t<VT, L, 4>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+  if (k <= 8) return launch_lanes_t<VT, L, 8>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+  return launch_lanes_t<VT, L, 16>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
 }
 
 template <typename VT>
 static cudaError_t lanes_dispatch(int lanes, int64_t n, const int32_t* rows, const int32_t* rp,
                                   const int32_t* col, const VT* val, const double* B, int64_t ldb, double* C,
-                                  int64_t ldc, int k, bool acc, cudaStream_t s) {
+                                  int64_t ldc, int k, bool acc, int pf, cudaStream_t s) {
   switch (lanes) {
-    case 1: return lanes_k<VT, 1>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-    case 2: return lanes_k<VT, 2>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-    case 4: return lanes_k<VT, 4>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-    case 8: return lanes_k<VT, 8>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-    case 16: return lanes_k<VT, 16>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
-    case 32: return lanes_k<VT, 32>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, s);
+    case 1: return lanes_k<VT, 1>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+    case 2: return lanes_k<VT, 2>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+    case 4: return lanes_k<VT, 4>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+    case 8: return lanes_k<VT, 8>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+    case 16: return lanes_k<VT, 16>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
+    case 32: return lanes_k<VT, 32>(n, rows, rp, col, val, B, ldb, C, ldc, k, acc, pf, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_crs_lanes(const CsrDev& A, bool fp32, int lanes, const double* B, int64_t ldb, double* C,
                              int64_t ldc, int k, cudaStream_t s) {
-  if (fp32) return lanes_dispatch<float>(lanes, A.n_rows, nullptr, A.row_ptr, A.col, A.val32, B, ldb, C, ldc, k,
-                                         false, s);
-  return lanes_dispatch<double>(lanes, A.n_rows, nullptr, A.row_ptr, A.col, A.val, B, ldb, C, ldc, k, false, s);
+  if (fp32 && A.val32_special)
+    return lanes_dispatch<float>(lanes, A.n_rows, nullptr, A.row_ptr, A.col, A.val32, B, ldb, C, ldc, k, false,
+                                 A.prefetch, s);
+  if (fp32)
+    return lanes_dispatch<f32n>(lanes, A.n_rows, nullptr, A.row_ptr, A.col, reinterpret_cast<const f32n*>(A.val32),
+                                B, ldb, C, ldc, k, false, A.prefetch, s);
+  return lanes_dispatch<double>(lanes, A.n_rows, nullptr, A.row_ptr, A.col, A.val, B, ldb, C, ldc, k, false,
+                                A.prefetch, s);
 }
 
 cudaError_t launch_halo(const HaloDev& H, bool fp32, const double* B, int64_t ldb, double* C, int64_t ldc, int k,
                         cudaStream_t s) {
-  if (fp32) return lanes_dispatch<float>(1, H.n_rows, H.rows, H.row_ptr, H.col, H.val32, B, ldb, C, ldc, k, true,
-                                         s);
-  return lanes_dispatch<double>(1, H.n_rows, H.rows, H.row_ptr, H.col, H.val, B, ldb, C, ldc, k, true, s);
+  if (fp32 && H.val32_special)
+    return lanes_dispatch<float>(1, H.n_rows, H.rows, H.row_ptr, H.col, H.val32, B, ldb, C, ldc, k, true, 0, s);
+  if (fp32)
+    return lanes_dispatch<f32n>(1, H.n_rows, H.rows, H.row_ptr, H.col, reinterpret_cast<const f32n*>(H.val32), B,
+                                ldb, C, ldc, k, true, 0, s);
+  return lanes_dispatch<double>(1, H.n_rows, H.rows, H.row_ptr, H.col, H.val, B, ldb, C, ldc, k, true, 0, s);
 }
 
 }  // namespace spmv

@@ -17,7 +17,21 @@ __global__ void __launch_bounds__(kThreads)
     k_sell(int64_t n_rows, int64_t n_chunks, const int32_t* __restrict__ perm,
            const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ chunk_len,
            const int32_t* __restrict__ col, const VT* __restrict__ val, const double* __restrict__ B,
-           int64_t ldb, double* __restrict__ C, int64_t ldc, int k) {
+           int64_t ldb, double* __restrict__ C, int64_t ldc, int k, int prefetch) {
+  constexpr int CPC = kThreads / kSellC;  // chunks per CTA
+  if (threadIdx.x == 0 && prefetch > 0) {
+    // bring the slots of the CTA `prefetch` positions ahead into L2 (chunk
+    // offsets are multiples of 32 slots, so the ranges are 16-byte aligned)
+    const int64_t c0 = ((int64_t)blockIdx.x + prefetch) * CPC;
+    if (c0 < n_chunks) {
+      const int64_t c1 = c0 + CPC < n_chunks ? c0 + CPC : n_chunks;
+      const int64_t s0 = __ldg(chunk_ptr + c0), s1 = __ldg(chunk_ptr + c1);
+      if (s1 > s0) {
+        prefetch_l2(val + s0, (uint32_t)((s1 - s0) * (int64_t)sizeof(VT)));
+        prefetch_l2(col + s0, (uint32_t)((s1 - s0) * 4));
+      }
+    }
+  }
   const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t c = r >> 5;
   if (c >= n_chunks) return;
@@ -27,29 +41,27 @@ __global__ void __launch_bounds__(kThreads)
   double acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0;
-  int j = 0;
-  for (; j + 2 <= len; j += 2) {
-    const int64_t s0 = base + (int64_t)j * kSellC, s1 = s0 + kSellC;
-    const double v0 = to_f64(ldcs(val + s0)), v1 = to_f64(ldcs(val + s1));
-    const double* b0 = B + (int64_t)ldcs(col + s0) * ldb;
-    const double* b1 = B + (int64_t)ldcs(col + s1) * ldb;
-    double g0[K], g1[K];
+  // batches of NB slots: all gathers of a batch are issued before its FMAs
+  constexpr int NB = K >= 4 ? 1 : 2;
+  for (int j = 0; j < len; j += NB) {
+    double v[NB];
+    const double* b[NB];
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      g0[q] = (q < k) ? __ldg(b0 + q) : 0.0;
-      g1[q] = (q < k) ? __ldg(b1 + q) : 0.0;
+    for (int u = 0; u < NB; ++u) {
+      const int64_t slot = base + (int64_t)((j + u < len) ? j + u : j) * kSellC;
+      v[u] = to_f64(ldcs(val + slot));
+      b[u] = B + (int64_t)ldcs(col + slot) * ldb;
     }
+    double g[NB][K];
 #pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (q < k) acc[q] = fma(v1, g1[q], fma(v0, g0[q], acc[q]));
-  }
-  if (j < len) {
-    const int64_t s0 = base + (int64_t)j * kSellC;
-    const double v0 = to_f64(ldcs(val + s0));
-    const double* b0 = B + (int64_t)ldcs(col + s0) * ldb;
+    for (int u = 0; u < NB; ++u)
 #pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (q < k) acc[q] = fma(v0, __ldg(b0 + q), acc[q]);
+      for (int q = 0; q < K; ++q) g[u][q] = (j + u < len && q < k) ? __ldg(b[u] + q) : 0.0;
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (j + u < len && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
   }
   if (r >= n_rows) return;
   double* out = C + (int64_t)__ldg(perm + r) * ldc;
@@ -65,7 +77,7 @@ static cudaError_t launch_sell_t(const SellDev& S, const VT* val, const double* 
   const int64_t threads = S.n_chunks * kSellC;
   const int64_t grid = (threads + kThreads - 1) / kThreads;
   k_sell<VT, K><<<(unsigned)grid, kThreads, 0, s>>>(S.n_rows, S.n_chunks, S.perm, S.chunk_ptr, S.chunk_len, S.col,
-                                                    val, B, ldb, C, ldc, k);
+                                                    val, B, ldb, C, ldc, k, S.prefetch);
   return cudaGetLastError();
 }
 
@@ -81,7 +93,8 @@ static cudaError_t sell_k(const SellDev& S, const VT* val, const double* B, int6
 
 cudaError_t launch_sell(const SellDev& S, bool fp32, const double* B, int64_t ldb, double* C, int64_t ldc, int k,
                         cudaStream_t s) {
-  if (fp32) return sell_k<float>(S, S.val32, B, ldb, C, ldc, k, s);
+  if (fp32 && S.val32_special) return sell_k<float>(S, S.val32, B, ldb, C, ldc, k, s);
+  if (fp32) return sell_k<f32n>(S, reinterpret_cast<const f32n*>(S.val32), B, ldb, C, ldc, k, s);
   return sell_k<double>(S, S.val, B, ldb, C, ldc, k, s);
 }
 

@@ -16,11 +16,6 @@
 
 namespace spmv {
 
-template <int K>
-struct Unroll {
-  static constexpr int value = K <= 2 ? 4 : (K <= 8 ? 2 : 1);
-};
-
 template <typename VT, int K>
 __device__ __forceinline__ void row_warp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                          const VT* __restrict__ val, int row, const double* __restrict__ B,
@@ -46,18 +41,44 @@ __device__ __forceinline__ void row_warp(const int32_t* __restrict__ row_ptr, co
     if (q < k && lane == q) out[q] = accumulate ? out[q] + acc[q] : acc[q];
 }
 
+// Entries of one row processed per batch: every gather of a batch is issued
+// before its FMAs, so short rows keep all their B loads in flight at once.
+template <int K>
+struct Batch {
+  static constexpr int value = K >= 4 ? 1 : 4 / K;
+};
+
+// Prefetch into L2 the val/col slices of row block `b` (called `prefetch`
+// blocks ahead of the block being processed).
+template <typename VT>
+__device__ __forceinline__ void prefetch_block(const uint32_t* __restrict__ blk, int64_t b,
+                                               const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                               const VT* __restrict__ val) {
+  const int r0 = (int)(__ldg(blk + b) & ~kBlockWarpFlag), r1 = (int)(__ldg(blk + b + 1) & ~kBlockWarpFlag);
+  const int bs = __ldg(row_ptr + r0), be = __ldg(row_ptr + r1);
+  if (be <= bs) return;
+  constexpr int VA = 16 / (int)sizeof(VT);
+  const int v_lo = bs & ~(VA - 1), v_hi = (be + VA - 1) & ~(VA - 1);
+  const int c_lo = bs & ~3, c_hi = (be + 3) & ~3;
+  prefetch_l2(val + v_lo, (uint32_t)(v_hi - v_lo) * (uint32_t)sizeof(VT));
+  prefetch_l2(col + c_lo, (uint32_t)(c_hi - c_lo) * 4u);
+}
+
 template <typename VT, int K>
 __global__ void __launch_bounds__(kThreads)
     k_crs_staged(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                 const VT* __restrict__ val, const uint32_t* __restrict__ blk, int tile,
-                 const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc, int k,
-                 int accumulate, int* __restrict__ status) {
+                 const VT* __restrict__ val, const uint32_t* __restrict__ blk, int64_t n_blk, int tile,
+                 int prefetch, const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc,
+                 int k, int accumulate, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
 
   const uint32_t e0 = __ldg(blk + blockIdx.x), e1 = __ldg(blk + blockIdx.x + 1);
   const int r0 = (int)(e0 & ~kBlockWarpFlag), r1 = (int)(e1 & ~kBlockWarpFlag);
   const int tid = threadIdx.x;
+
+  if (tid == 32 && prefetch > 0 && (int64_t)blockIdx.x + prefetch < n_blk)
+    prefetch_block(blk, (int64_t)blockIdx.x + prefetch, row_ptr, col, val);
 
   if (e0 & kBlockWarpFlag) {  // block of long rows: one warp per row
     const int row = r0 + (tid >> 5);
@@ -102,33 +123,26 @@ __global__ void __launch_bounds__(kThreads)
   double acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0;
-  constexpr int U = Unroll<K>::value;
-  int j = rs;
-  for (; j + U <= re; j += U) {
-    double v[U];
-    const double* b[U];
+  constexpr int NB = Batch<K>::value;
+  for (int j = rs; j < re; j += NB) {
+    double v[NB];
+    const double* b[NB];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      v[u] = to_f64(sval[j + u - v_lo]);
-      b[u] = B + (int64_t)scol[j + u - c_lo] * ldb;
+    for (int u = 0; u < NB; ++u) {
+      const int jj = (j + u < re) ? j + u : j;
+      v[u] = to_f64(sval[jj - v_lo]);
+      b[u] = B + (int64_t)scol[jj - c_lo] * ldb;
     }
-    double g[U][K];
+    double g[NB][K];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < NB; ++u)
 #pragma unroll
-      for (int q = 0; q < K; ++q) g[u][q] = (q < k) ? __ldg(b[u] + q) : 0.0;
+      for (int q = 0; q < K; ++q) g[u][q] = (j + u < re && q < k) ? __ldg(b[u] + q) : 0.0;
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < NB; ++u)
 #pragma unroll
       for (int q = 0; q < K; ++q)
-        if (q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
-  }
-  for (; j < re; ++j) {
-    const double v = to_f64(sval[j - v_lo]);
-    const double* b = B + (int64_t)scol[j - c_lo] * ldb;
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+        if (j + u < re && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
   }
   double* out = C + (int64_t)row * ldc;
 #pragma unroll
@@ -141,10 +155,17 @@ static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double*
                                    int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
   const size_t smem = sizeof(VT) * (size_t)(A.tile + 8) + 4 * (size_t)(A.tile + 8);
   auto kern = k_crs_staged<VT, K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static int smem_set[64] = {0};  // per device: largest dynamic shared memory size enabled so far
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)A.n_blk, kThreads, smem, s>>>(A.row_ptr, A.col, val, A.blk, A.tile, B, ldb, C, ldc, k,
-                                                  accumulate ? 1 : 0, status);
+  if (dev >= 64 || (int)smem > smem_set[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) smem_set[dev] = (int)smem;
+  }
+  kern<<<(unsigned)A.n_blk, kThreads, smem, s>>>(A.row_ptr, A.col, val, A.blk, A.n_blk, A.tile, A.prefetch, B,
+                                                  ldb, C, ldc, k, accumulate ? 1 : 0, status);
   return cudaGetLastError();
 }
 
@@ -161,7 +182,10 @@ static cudaError_t dispatch_staged(const CsrDev& A, const VT* val, const double*
 cudaError_t launch_crs_staged(const CsrDev& A, bool fp32, const double* B, int64_t ldb, double* C,
                               int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
   if (A.n_blk == 0) return cudaSuccess;
-  if (fp32) return dispatch_staged<float>(A, A.val32, B, ldb, C, ldc, k, accumulate, status, s);
+  if (fp32 && A.val32_special) return dispatch_staged<float>(A, A.val32, B, ldb, C, ldc, k, accumulate, status, s);
+  if (fp32)
+    return dispatch_staged<f32n>(A, reinterpret_cast<const f32n*>(A.val32), B, ldb, C, ldc, k, accumulate, status,
+                                 s);
   return dispatch_staged<double>(A, A.val, B, ldb, C, ldc, k, accumulate, status, s);
 }
 

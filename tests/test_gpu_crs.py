@@ -104,12 +104,19 @@ def test_fp32_values(lib, variant):
         assert_close(yk, A, Bk, tol=TOL_FP32VAL)
 
 
-@pytest.mark.parametrize("variant", [VARIANTS[0], VARIANTS[1], VARIANTS[7]], ids=["crs_staged", "crs_l1", "sell"])
-def test_fp32_widening_special_values(lib, variant):
-    """The integer-pipe float->double widening is exact for zeros of both signs,
-    normals across the exponent range, and subnormal floats."""
-    vals = np.array([0.0, -0.0, 1.0, -1.0, 3.1415926535, 1e-30, -2.5e30, 3.4e38, 1.2e-38, 1e-40, -7e-45,
-                     1.17549435e-38, 6.0e-39, 123456.789, -0.1], dtype=np.float64)
+@pytest.mark.parametrize("subnormals", [False, True], ids=["normal_only", "with_subnormals"])
+@pytest.mark.parametrize("variant", [VARIANTS[0], VARIANTS[1], VARIANTS[2], VARIANTS[7]],
+                         ids=["crs_staged", "crs_l1", "crs_l2", "sell"])
+def test_fp32_widening_special_values(lib, variant, subnormals):
+    """FP32 storage widens exactly: the integer-pipe path (zeros of both signs and
+    normals across the exponent range, including the smallest and largest
+    normal floats) and the hardware path the plan picks when subnormal floats
+    are present."""
+    vals = [0.0, -0.0, 1.0, -1.0, 3.1415926535, 1e-30, -2.5e30, 3.4e38, 1.2e-38, 1.17549435e-38,
+            -3.4028234e38, 123456.789, -0.1]
+    if subnormals:
+        vals += [1e-40, -7e-45, 6.0e-39]
+    vals = np.array(vals, dtype=np.float64)
     n = len(vals)
     A = gen.CSR(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), vals)
     B = np.ones(n)
@@ -174,7 +181,8 @@ def test_set_variant_switches(lib):
     A = case("poisson40")
     B = gen.uniform(A.n_cols, seed=4)
     with lib.Plan.from_csr(A) as p:
-        assert p.info().variant == lib.SPMV_CRS_STAGED
+        assert p.info().variant == lib.SPMV_CRS_L1   # the default (AUTO) kernel
+        assert p.tuning().prefetch_distance == 152
         for _, vid, sig in VARIANTS:
             p.set_variant(vid, sig)
             assert p.info().variant == vid
@@ -203,3 +211,18 @@ def test_error_paths(lib):
             p.sell_export()
         assert e.value.status == 6
         p.check()
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_prefetch_tuning_keeps_results(lib, variant):
+    """The L2 prefetch distance is a pure performance knob: results are identical."""
+    A = case("eigen")
+    B = gen.uniform(A.n_cols, seed=21)
+    with make(lib, A, variant[1], variant[2]) as p:
+        base = run(p, B)
+        for d in (1, 7, 300, 100000):
+            p.set_tuning(prefetch_distance=d)
+            assert p.tuning().prefetch_distance == d
+            assert np.array_equal(run(p, B), base)
+        with pytest.raises(lib.SpmvError):
+            p.set_tuning(prefetch_distance=-1)
