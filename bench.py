@@ -1,20 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark of the CRS spMVM C = A*B on GB300.
 
-Workload (default): the 3D 7-point variable-coefficient Poisson stencil on a
+Default workload: the 3D 7-point variable-coefficient Poisson stencil on a
 280^3 grid (N = 21,952,000 rows, 153,193,600 nonzeros, FP64 CRS), the stand-in
 for the paper's sAMG matrix.  One step = one product C = A*B with the plan's
-default kernel (CRS_L1: thread per row, val/col slices of the CTA 152 positions
-ahead prefetched into L2 by the TMA engine).  Inputs (2.28 GB) exceed L2
-(129 MB), so no flush is needed between steps.
+default kernel (CRS_L1: thread per row; the val/col slices of the CTA 152
+positions ahead are prefetched into L2 by the TMA engine).  Inputs (2.28 GB)
+exceed L2 (129 MB), so no flush is needed between steps.
+
+--workload powerlaw_batch512: 512 uneven power-law matrices with k = 4
+right-hand sides each, one step = one batched persistent launch (graph
+replay) with the adaptive row policy and the autotuned configuration.
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
-Under torchrun each rank runs an independent replica (the path does not shard
-over GPUs here) and `value` is the sum over ranks.
+Under torchrun each rank runs an independent replica (the product does not
+shard over GPUs here) and `value` is the sum over ranks.
 """
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -30,25 +35,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spMVM GFlop/s & HBM GB/s vs roofline; chosen form vs plain CRS at stated err"
 WORKLOADS = {
-    "poisson3d_280": "3D 7-point variable-coefficient Poisson stencil, 280^3 grid, N=21,952,000, nnz=153,193,600, FP64 CRS, B~U[-1,1) seed 0",
-    "poisson3d_160": "3D 7-point variable-coefficient Poisson stencil, 160^3 grid, N=4,096,000, nnz=28,518,400, FP64 CRS (profiling size)",
+    "poisson3d_280": "3D 7-point variable-coefficient Poisson stencil, 280^3 grid, N=21,952,000, nnz=153,193,600, "
+                     "FP64 CRS, B~U[-1,1) seed 0",
+    "poisson3d_160": "3D 7-point variable-coefficient Poisson stencil, 160^3 grid, N=4,096,000, nnz=28,518,400, "
+                     "FP64 CRS (profiling size)",
     "eigen_6201600": "symmetric eigenproblem-shaped matrix, N=6,201,600 (400 x 15,504), ~13.8 nnz/row, FP64 CRS",
+    "laplace2d_256": "2D 5-point Laplacian 256^2, N=65,536, nnz=326,656, FP64 CRS (L2 resident)",
+    "powerlaw_batch512": "512 matrices, N log-uniform in [1e3,2e5], power-law rows (alpha 2.2, 1..2000), "
+                         "uniform columns, k=4 RHS each, one persistent graph-captured launch",
 }
 VARIANTS = {"crs_staged": (1, 1), "crs_l1": (2, 1), "crs_l2": (3, 1), "crs_l4": (4, 1), "crs_l8": (5, 1),
             "crs_l16": (6, 1), "crs_l32": (7, 1), "sell_s1": (8, 1), "sell_s256": (8, 256), "sell_s4096": (8, 4096)}
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson3d_280", choices=sorted(WORKLOADS))
     ap.add_argument("--variant", default="crs_l1", choices=sorted(VARIANTS))
     ap.add_argument("--fp32-val", action="store_true", help="store val in FP32 (FP64 accumulation)")
+    ap.add_argument("--k", type=int, default=1, help="right-hand sides per product (single-matrix workloads)")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--no-forms", action="store_true", help="skip the comparison of forms")
     return ap.parse_args()
 
 
@@ -62,27 +78,34 @@ def load_workload(name):
         A = gen.poisson3d_var(int(name.split("_")[1]), seed=0)
     elif name == "eigen_6201600":
         A = gen.eigen_shaped(6_201_600, seed=0)
+    elif name == "laplace2d_256":
+        A = gen.laplace2d(256)
     else:
         raise ValueError(name)
-    return A, gen.uniform(A.n_cols, seed=0)
+    return A
 
 
-def measured_peaks():
+def measured_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
-def kernel_fingerprint() -> str:
+def kernel_fingerprint(files) -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1101_0091_gb300", "csrc"))):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1101_0091_gb300", "csrc", f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"crs_l1": ["k_lanes.cu", "device.cuh", "internal.h"],
+                  "crs_staged": ["k_staged.cu", "device.cuh", "internal.h"],
+                  "sell": ["k_sell.cu", "device.cuh", "internal.h"],
+                  "batch": ["batch_kernel.cuh", "batch.cu", "device.cuh", "internal.h"]}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -94,20 +117,21 @@ def ncu_traffic(kernel: str, workload: str):
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"{kernel}/{workload}")
-    if not e or e.get("source_fingerprint") != kernel_fingerprint():
+    src = KERNEL_SOURCES.get(kernel.split("_s")[0] if kernel.startswith("sell") else kernel)
+    if not e or not src or e.get("source_fingerprint") != kernel_fingerprint(src):
         return None
     return e.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling of SM clocks and throttle reasons; summary() keeps
+    the samples taken inside [t0, t1] (host wall clock)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
+        self.index, self.proc, self.lines = index, None, []
 
     def __enter__(self):
         try:
@@ -119,9 +143,8 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
-            time.sleep(0.25)
+            time.sleep(0.3)
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
@@ -130,16 +153,20 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    def summary(self, t0: float, t1: float):
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
+        for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if not (t0 - 0.05 <= ts <= t1 + 0.05):
+                    continue
+                sm.append(float(f[2]))
+                mx.append(float(f[3]))
+                pw.append(float(f[4]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -147,45 +174,296 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_median": statistics.median(pw),
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def time_oracle(A, B, steps: int, budget_s: float = 20.0):
-    """Time the oracle's plain FP64 loop (single thread) on the full product,
-    at most `steps` runs or `budget_s` seconds."""
-    import oracle
-    oracle.spmv(A, B)  # load / warm
+def time_oracle(fn, steps: int, budget_s: float):
+    fn()
     ts = []
     t_end = time.perf_counter() + budget_s
     for _ in range(max(1, steps)):
         t0 = time.perf_counter()
-        oracle.spmv(A, B)
+        fn()
         ts.append(time.perf_counter() - t0)
         if time.perf_counter() > t_end:
             break
     return ts
 
 
+def batch_members(count):
+    import gen
+    As = [gen.powerlaw_batch_member(m) for m in range(count)]
+    Bs = [gen.rhs_block(A.n_cols, 4, seed=0, stream=2 * m + 1) for m, A in enumerate(As)]
+    return As, Bs
+
+
 def reference_arm(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    A, B = load_workload(args.workload)
-    flops = 2 * A.nnz
-    ts = time_oracle(A, B, args.steps + args.warmup, budget_s=120.0)
-    ts = ts[min(args.warmup, len(ts) - 1):] if len(ts) > 1 else ts
+    import gen
+    import oracle
+    if args.workload.startswith("powerlaw_batch"):
+        As, Bs = batch_members(args.batch_count)
+        flops = sum(8 * A.nnz for A in As)
+        fn = lambda: [oracle.spmm(A, B) for A, B in zip(As, Bs)]  # noqa: E731
+        sample = f"all {len(As)} members, k=4, single-threaded FP64 oracle loop"
+    else:
+        A = load_workload(args.workload)
+        B = gen.uniform(A.n_cols, seed=0)
+        flops = 2 * A.nnz
+        fn = lambda: oracle.spmv(A, B)  # noqa: E731
+        sample = "full product, single-threaded FP64 oracle loop"
+    ts = time_oracle(fn, max(1, min(args.steps, 20)), budget_s=90.0)
     t = sum(ts) / len(ts)
     value = flops / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFlop/s", "n_gpus": args.gpus,
-            "steps": len(ts), "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+            "steps": len(ts), "warmup": 1, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
             "cpu_baseline": {"value": round(value, 4), "unit": "GFlop/s", "cores": 1, "kind": "oracle",
-                             "sample": f"full product, {len(ts)} timed runs of the single-threaded FP64 CRS loop"},
+                             "sample": f"{sample}, {len(ts)} timed runs"},
             "e2e": {"value": round(value, 4), "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+class Timer:
+    """CUDA-event timing of `steps` calls on one stream, with a barrier and a
+    synchronize on both sides and nvidia-smi clock samples inside the region."""
+
+    def __init__(self, torch, stream, world, local):
+        self.torch, self.stream, self.world, self.local = torch, stream, world, local
+
+    def barrier(self):
+        self.torch.cuda.synchronize()
+        if self.world > 1:
+            self.torch.distributed.barrier()
+            self.torch.cuda.synchronize()
+
+    def run(self, fn, steps, warmup, sample_clocks=False):
+        torch = self.torch
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        clk = ClockSampler(self.local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
+        t_warm = time.perf_counter() + (0.8 if clk else 0.0)
+        i = 0
+        while i < warmup or time.perf_counter() < t_warm:   # warm-up; also lets the sampler start
+            fn()
+            i += 1
+            if i % 50 == 0:
+                self.stream.synchronize()
+        self.barrier()
+        t0 = time.time()
+        ev[0].record(self.stream)
+        for s in range(steps):
+            fn()
+            ev[s + 1].record(self.stream)
+        self.stream.synchronize()
+        t1 = time.time()
+        self.barrier()
+        if clk:
+            clk.__exit__(None, None, None)
+        per = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        if self.world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return {"total_ms": total_ms, "per_ms": per, "wall_s": t1 - t0,
+                "clocks": clk.summary(t0, t1) if clk else None}
+
+
+def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
+    import gen
+    A = load_workload(args.workload)
+    k = args.k
+    Bh = gen.uniform(A.n_cols, seed=0) if k == 1 else gen.rhs_block(A.n_cols, k, seed=0)
+    vid, sigma = VARIANTS[args.variant]
+    plan = spmv.Plan.from_csr(A, variant=vid, sell_sigma=sigma, val_fp32=args.fp32_val)
+    B = torch.from_numpy(Bh).cuda()
+    C = torch.empty((A.n_rows,) if k == 1 else (A.n_rows, k), dtype=torch.float64, device="cuda")
+    stream.wait_stream(torch.cuda.current_stream())
+    fn = (lambda: plan.apply(B, C, stream)) if k == 1 else (lambda: plan.apply_block(B, C, k, stream))
+    tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k, val_bytes=4 if args.fp32_val else 8)
+    r = timer.run(fn, args.steps, args.warmup, sample_clocks=True)
+    plan.check(stream)
+    t_step = r["total_ms"] / 1e3 / args.steps
+    kern_s = statistics.mean(r["per_ms"]) / 1e3
+    hbm, hbm_kind = measured_hbm()
+    achieved = tr.bytes_min / kern_s / 1e9
+    kname = "sell" if args.variant.startswith("sell") else args.variant
+    line = {
+        "metric": METRIC, "value": round(tr.flops * world / t_step / 1e9, 3), "unit": "GFlop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": args.variant,
+                   "val_storage": "f32" if args.fp32_val else "f64", "k": k, "n_rows": A.n_rows, "nnz": A.nnz,
+                   "l2": (f"inputs larger than L2 ({tr.bytes_min / 1e9:.2f} GB vs 129 MB), no flush"
+                          if tr.bytes_min > 2 * 129e6 else "inputs L2-resident (warm figure)"),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "hbm_gbs": round(achieved, 1),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_kind": hbm_kind,
+                     "traffic": ncu_traffic(kname, args.workload),
+                     "algorithmic_bytes_per_launch": tr.bytes_min,
+                     "fp64_frac": round(tr.flops / kern_s / 1e9 / FP64_PEAK_GFLOPS, 4)},
+        "gpu_launches": args.steps,
+        "clocks": r["clocks"],
+        "wall_s_timed": round(r["wall_s"], 4),
+    }
+    if not args.no_e2e:
+        # through the C ABI from pinned host buffers: H2D of B and D2H of C inside the timed region
+        Bpin = torch.from_numpy(np.ascontiguousarray(Bh)).pin_memory()
+        Cpin = torch.empty(C.shape, dtype=torch.float64).pin_memory()
+        n_e2e = max(3, min(args.steps, 20))
+        for _ in range(2):
+            plan.apply_host_ptr(Bpin.data_ptr(), k, Cpin.data_ptr(), stream)
+        timer.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.apply_host_ptr(Bpin.data_ptr(), k, Cpin.data_ptr(), stream)
+        e2e_t = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([e2e_t], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        line["e2e"] = {"value": round(tr.flops * world / e2e_t / 1e9, 3), "unit": "GFlop/s",
+                       "h2d_bytes_per_step": 8 * A.n_cols * k, "d2h_bytes_per_step": 8 * A.n_rows * k}
+    if not args.no_forms and args.workload.startswith("poisson3d"):
+        line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        ts = time_oracle(lambda: oracle.spmv(A, Bh) if k == 1 else oracle.spmm(A, Bh), 3, budget_s=30.0)
+        line["cpu_baseline"] = {"value": round(tr.flops / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                                "kind": "oracle", "sample": f"full product, best of {len(ts)} single-threaded runs"}
+    plan.close()
+    return line
+
+
+def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
+    """Chosen forms vs plain CRS on the same matrix (median event time of 200 steps)."""
+    forms = {}
+    tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz)
+
+    def med(fn, steps=200):
+        return statistics.median(timer.run(fn, steps, 10)["per_ms"]) / 1e3
+
+    for name in ("crs_l1", "crs_staged", "sell_s256"):
+        vid, sigma = VARIANTS[name]
+        plan.set_variant(vid, sigma)
+        t = med(lambda: plan.apply(B, C, stream))
+        forms[name] = {"gflops": round(tr.flops / t / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t / 1e9, 1)}
+    plan.set_variant(*VARIANTS["crs_l1"])
+    with spmv.Plan.from_csr(A, val_fp32=True) as p32:
+        t = med(lambda: p32.apply(B, C, stream))
+        tr32 = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4)
+        forms["crs_l1_fp32val"] = {"gflops": round(tr.flops / t / 1e9, 1),
+                                   "hbm_gbs": round(tr32.bytes_min / t / 1e9, 1), "err_bound": "2e-7*sum|ab|"}
+    # local/halo split: last 10% of the columns copied from pinned host memory on a side stream
+    h = A.n_cols - A.n_cols // 10
+    with spmv.Plan.from_csr(A, halo_begin=h) as ps:
+        halo = torch.from_numpy(Bh[h:].copy()).pin_memory()
+        cs = torch.cuda.Stream()
+        t_ov = med(lambda: ps.apply_split(B, halo, C, stream, cs), 100)
+        t_ser = med(lambda: ps.apply_split(B, halo, C, stream, stream), 100)
+        info = ps.info()
+        forms["split_overlapped"] = {"gflops": round(tr.flops / t_ov / 1e9, 1), "ms": round(t_ov * 1e3, 4),
+                                     "halo_bytes_h2d": 8 * (A.n_cols - h), "n_halo_rows": info.n_halo_rows}
+        forms["split_serial_copy"] = {"gflops": round(tr.flops / t_ser / 1e9, 1), "ms": round(t_ser * 1e3, 4)}
+        forms["split_penalty_eq2_model"] = round(pm.split_penalty(A.nnz / A.n_rows), 4)
+    return forms
+
+
+def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
+    As, Bhs = batch_members(args.batch_count)
+    nnz = sum(A.nnz for A in As)
+    rows = sum(A.n_rows for A in As)
+    flops = 8 * nnz
+    plans = [spmv.Plan.from_csr(A) for A in As]
+    Bs = [torch.from_numpy(B).cuda() for B in Bhs]
+    Cs = [torch.empty((A.n_rows, 4), dtype=torch.float64, device="cuda") for A in As]
+    stream.wait_stream(torch.cuda.current_stream())
+    batch = spmv.Batch(plans, 4, [spmv.SPMV_BATCH_ADAPT] * len(As))
+    batch.set_io(Bs, Cs)
+    tuned = None
+    if not args.no_autotune:
+        best, times = batch.autotune(stream, reps=3)
+        tuned = {"item_nnz": best.item_nnz, "schedule": ["static", "atomic"][best.schedule],
+                 "ctas_per_sm": best.ctas_per_sm}
+    r = timer.run(lambda: batch.apply(stream), args.steps, args.warmup, sample_clocks=True)
+    t_step = r["total_ms"] / 1e3 / args.steps
+    kern_s = statistics.mean(r["per_ms"]) / 1e3
+    bytes_min = sum(pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=4).bytes_min for A in As)
+    hbm, hbm_kind = measured_hbm()
+    achieved_gf = flops / kern_s / 1e9
+    line = {
+        "metric": METRIC, "value": round(flops * world / t_step / 1e9, 3), "unit": "GFlop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "members": len(As),
+                   "rows": rows, "nnz": nnz, "k": 4, "kernel": "k_batch (adaptive row policy, graph replay)",
+                   "autotuned": tuned, "l2": "inputs larger than L2, no flush",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "hbm_gbs": round(bytes_min / kern_s / 1e9, 1),
+        "roofline": {"bound": "alu", "achieved": round(achieved_gf, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                     "unit": "GFLOP/s", "frac": round(achieved_gf / FP64_PEAK_GFLOPS, 4),
+                     "peak_kind": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                     "traffic": ncu_traffic("batch", args.workload), "algorithmic_bytes_per_launch": bytes_min,
+                     "hbm_frac": round(bytes_min / kern_s / 1e9 / hbm, 4), "hbm_peak": hbm, "hbm_peak_kind": hbm_kind},
+        "gpu_launches": args.steps,
+        "clocks": r["clocks"],
+        "wall_s_timed": round(r["wall_s"], 4),
+    }
+    if not args.no_e2e:
+        # end to end through the C ABI: every step copies all members' B in from pinned host memory,
+        # runs the batched launch, and copies all C back
+        Bpin = [torch.from_numpy(B).pin_memory() for B in Bhs]
+        Cpin = [torch.empty((A.n_rows, 4), dtype=torch.float64).pin_memory() for A in As]
+        n_e2e = 5
+
+        def step():
+            with torch.cuda.stream(stream):
+                for Bd, Bp in zip(Bs, Bpin):
+                    Bd.copy_(Bp, non_blocking=True)
+                batch.apply(stream)
+                for Cd, Cp in zip(Cs, Cpin):
+                    Cp.copy_(Cd, non_blocking=True)
+            stream.synchronize()
+        step()
+        timer.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            step()
+        e2e_t = (time.perf_counter() - t0) / n_e2e
+        line["e2e"] = {"value": round(flops * world / e2e_t / 1e9, 3), "unit": "GFlop/s",
+                       "h2d_bytes_per_step": sum(8 * B.size for B in Bhs),
+                       "d2h_bytes_per_step": sum(32 * A.n_rows for A in As)}
+    if not args.no_forms:
+        forms = {}
+        def med(fn, steps=20):
+            return statistics.median(timer.run(fn, steps, 3)["per_ms"]) / 1e3
+        forms["batched_adaptive_tuned"] = {"gflops": round(flops / kern_s / 1e9, 1)}
+        t = med(lambda: batch.apply_separate(stream), 3)
+        forms["separate_launches_plan_default"] = {"gflops": round(flops / t / 1e9, 2), "launches": len(As)}
+        for pol in range(spmv.SPMV_BATCH_N_POLICIES - 1):
+            batch.set_policies([pol] * len(As))
+            t = med(lambda: batch.apply(stream))
+            forms[f"batched_fixed_{spmv.POLICY_NAMES[pol]}"] = {"gflops": round(flops / t / 1e9, 1)}
+        line["forms"] = forms
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        sub = min(len(As), 64)
+        ts = time_oracle(lambda: [oracle.spmm(A, B) for A, B in zip(As[:sub], Bhs[:sub])], 1, budget_s=30.0)
+        fl = sum(8 * A.nnz for A in As[:sub])
+        line["cpu_baseline"] = {"value": round(fl / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                                "kind": "oracle", "sample": f"first {sub} members, k=4, best of {len(ts)}"}
+    batch.close()
+    for p in plans:
+        p.close()
+    return line
 
 
 def main():
@@ -198,101 +476,19 @@ def main():
 
     rank, world, local = dist_info()
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        torch.distributed.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
     spmv.load()
-    A, Bh = load_workload(args.workload)
-    vid, sigma = VARIANTS[args.variant]
-    plan = spmv.Plan.from_csr(A, variant=vid, sell_sigma=sigma, val_fp32=args.fp32_val)
     stream = torch.cuda.Stream()
-    B = torch.from_numpy(Bh).cuda()
-    C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
-    traffic = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4 if args.fp32_val else 8)
-    hbm_peak, peak_kind = measured_peaks()
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    stream.wait_stream(torch.cuda.current_stream())
-    for _ in range(args.warmup):
-        plan.apply(B, C, stream)
-    plan.check(stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        ev[0].record(stream)
-        for i in range(args.steps):
-            plan.apply(B, C, stream)
-            ev[i + 1].record(stream)
-        stream.synchronize()
-        wall = time.perf_counter() - t0
-    barrier()
-    plan.check(stream)
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    t_step = total_ms / 1e3 / args.steps
-    flops_all = traffic.flops * world
-    value = flops_all / t_step / 1e9
-    kern_s = statistics.mean(per) / 1e3
-    achieved = traffic.bytes_min / kern_s / 1e9
-
-    # end to end through the C ABI from pinned host buffers (H2D of B, D2H of C inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        Bpin = torch.from_numpy(Bh).pin_memory()
-        Cpin = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
-        for _ in range(2):
-            plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
-        e2e_steps = max(3, min(args.steps, 20))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            plan.apply_host_ptr(Bpin.data_ptr(), 1, Cpin.data_ptr(), stream)
-        e2e_t = (time.perf_counter() - t0) / e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_t], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_t = float(t.item())
-        e2e = {"value": round(flops_all / e2e_t / 1e9, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 8 * A.n_cols,
-               "d2h_bytes_per_step": 8 * A.n_rows}
-
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": args.variant,
-                   "val_storage": "f32" if args.fp32_val else "f64", "n_rows": A.n_rows, "nnz": A.nnz,
-                   "l2": f"inputs larger than L2 ({traffic.bytes_min / 1e9:.2f} GB vs 129 MB), no flush",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "hbm_gbs": round(achieved, 1),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(args.variant, args.workload),
-                     "algorithmic_bytes_per_launch": traffic.bytes_min},
-        "e2e": e2e,
-        "gpu_launches": args.steps,
-        "clocks": clk.summary(),
-        "wall_s_timed": round(wall, 4),
-    }
-    if rank == 0 and not args.no_cpu:
-        ts = time_oracle(A, Bh, 3)
-        tc = min(ts)
-        line["cpu_baseline"] = {"value": round(traffic.flops / tc / 1e9, 4), "unit": "GFlop/s", "cores": 1,
-                                "kind": "oracle", "sample": f"full product, best of {len(ts)} single-threaded runs"}
+    timer = Timer(torch, stream, world, local)
+    if args.workload.startswith("powerlaw_batch"):
+        line = batch_workload(args, torch, spmv, pm, timer, stream, world, rank)
+    else:
+        line = single_workload(args, torch, spmv, pm, timer, stream, world, rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -177,6 +177,81 @@ spmv_status spmv_split_export(spmv_handle h, int32_t* loc_row_ptr, int32_t* loc_
                               double* halo_val);
 
 /* ----------------------------------------------------------------------------
+ * Batched products: many uneven matrices, each with a block of k right-hand
+ * sides, in ONE persistent kernel launch replayed from a CUDA graph.  Each
+ * member computes C_m = A_m * B_m with the loop of Sec. 1.2 (row-major blocks,
+ * ldb_m/ldc_m >= k).  The work list holds items (matrix, row range, lanes per
+ * row L); warps of a grid of (SMs x resident CTAs) take items either in a fixed
+ * round-robin order or from an atomic counter, and L lanes share a row (an
+ * xor-shuffle tree adds their partial sums when L > 1).  The batch keeps
+ * pointers to the members' device arrays: the plans must outlive the batch.
+ * ------------------------------------------------------------------------- */
+
+/* Per-matrix row policy of a batch member (the "variant" of a member). */
+typedef enum {
+  SPMV_BATCH_L1 = 0,      /* one lane per row                                        */
+  SPMV_BATCH_L2 = 1,
+  SPMV_BATCH_L4 = 2,
+  SPMV_BATCH_L8 = 3,
+  SPMV_BATCH_L32 = 4,     /* a warp per row                                          */
+  SPMV_BATCH_ADAPT = 5,   /* per row: L = smallest power of two >= len/4, at most 32; */
+                          /* consecutive rows of equal L share an item               */
+  SPMV_BATCH_N_POLICIES = 6
+} spmv_batch_policy;
+
+typedef struct {
+  int32_t item_nnz;       /* target nonzeros per work item (64 .. 1<<20)              */
+  int32_t schedule;       /* 0 = static round-robin over warps, 1 = atomic counter     */
+  int32_t ctas_per_sm;    /* persistent grid = SMs x ctas_per_sm (1 .. 8)              */
+  int32_t reserved[5];
+} spmv_batch_config;
+
+/* Default batch configuration: item_nnz 1024, atomic counter, 8 CTAs per SM. */
+spmv_batch_config spmv_batch_default_config(void);
+
+/* Build a batch over `count` plans (same device) with k right-hand sides each
+ * (1 <= k <= 16).  policies[count] (NULL: all ADAPT) picks each member's row
+ * policy.  Uploads the work list and the member table; no product runs. */
+spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_handle* plans, int32_t k,
+                              const int32_t* policies, const spmv_batch_config* cfg);
+
+/* Set the members' operands: B_ptrs[m] (n_cols_m x ldb[m]) and C_ptrs[m]
+ * (n_rows_m x ldc[m]) are DEVICE pointers held in host arrays; ldb/ldc NULL
+ * means k.  Copied to the device member table (synchronously); call again to
+ * move the batch to other buffers. */
+spmv_status spmv_batch_set_io(spmv_batch_handle b, const double* const* B_ptrs, const int64_t* ldb,
+                              double* const* C_ptrs, const int64_t* ldc);
+
+/* Enqueue the whole batch on `stream`: replays the batch's CUDA graph (counter
+ * reset + persistent kernel).  Asynchronous. */
+spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream);
+
+/* Same work as separate launches: one kernel per member, in member order (the
+ * baseline the batched launch replaces).  Asynchronous. */
+spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream);
+
+/* Change the configuration (rebuilds the work list and the graph). */
+spmv_status spmv_batch_set_config(spmv_batch_handle b, const spmv_batch_config* cfg);
+spmv_status spmv_batch_get_config(spmv_batch_handle b, spmv_batch_config* cfg);
+
+/* Change the members' policies (rebuilds the work list and the graph). */
+spmv_status spmv_batch_set_policies(spmv_batch_handle b, const int32_t* policies);
+
+/* Autotuner: times every configuration of item_nnz in {256, 512, 1024, 2048,
+ * 4096} x schedule in {static, atomic} x ctas_per_sm in {4, 8} (`reps` graph
+ * replays each after one warm-up, CUDA events on `stream`; needs set_io
+ * first), keeps the fastest, and returns it (best may be NULL).  times_ms
+ * (NULL or 20 entries) receives the median time of each configuration in that
+ * order.  Results do not depend on the configuration. */
+spmv_status spmv_batch_autotune(spmv_batch_handle b, void* stream, int32_t reps, spmv_batch_config* best,
+                                float* times_ms);
+
+/* Number of work items in the current work list. */
+spmv_status spmv_batch_info(spmv_batch_handle b, int64_t* n_items, int64_t* total_rows, int64_t* total_nnz);
+
+spmv_status spmv_batch_destroy(spmv_batch_handle b);
+
+/* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).
  * out[34] (float64) for HOST CRS arrays and k right-hand sides:
  *   [0:13]  fraction of rows in length bin b: b(L) = 0 for L = 0, else

@@ -21,6 +21,13 @@ from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_bl
                        SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
                        SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_N_VARIANTS)
 
+from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV_BATCH_L1,  # noqa: F401,E402
+                             SPMV_BATCH_L2, SPMV_BATCH_L4, SPMV_BATCH_L8, SPMV_BATCH_L32, SPMV_BATCH_N_POLICIES,
+                             Batch, spmv_batch_apply, spmv_batch_apply_separate, spmv_batch_autotune,
+                             spmv_batch_config, spmv_batch_create, spmv_batch_default_config, spmv_batch_destroy,
+                             spmv_batch_get_config, spmv_batch_info, spmv_batch_set_config, spmv_batch_set_io,
+                             spmv_batch_set_policies)
+
 LANE_VARIANTS = {1: SPMV_CRS_L1, 2: SPMV_CRS_L2, 4: SPMV_CRS_L4, 8: SPMV_CRS_L8, 16: SPMV_CRS_L16,
                  32: SPMV_CRS_L32}
 

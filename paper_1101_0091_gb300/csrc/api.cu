@@ -116,6 +116,12 @@ static void apply_tuning(spmv_plan* p) {
   p->sell.prefetch = p->tuning.prefetch_distance;
 }
 
+namespace spmv {
+const CsrDev* plan_csr(spmv_handle h) { return &h->A; }
+const int32_t* plan_host_row_ptr(spmv_handle h) { return h->host.row_ptr.data(); }
+int plan_device(spmv_handle h) { return h->device; }
+}  // namespace spmv
+
 static spmv_status build_blocks(spmv_plan* p, CsrDev* M, const int32_t* host_row_ptr) {
   int tile = 0;
   std::vector<uint32_t> blk = build_row_blocks(host_row_ptr, M->n_rows, kStagedRows, kLongRow, &tile);

@@ -1,0 +1,398 @@
+// Batched products over many uneven matrices in one persistent launch,
+// replayed from a CUDA graph, and the autotuner of its launch configuration.
+//
+// Work list: items (matrix, rows, lanes per row L).  A persistent grid of
+// SMs x ctas_per_sm CTAs runs; each warp takes items either round-robin
+// (static) or from an atomic counter reset by the graph before the kernel
+// (dynamic).  Inside an item, groups of L lanes share a row (Sec. 1.2 loop per
+// lane over a strided subset of the row, FP64 FMAs, xor-shuffle sum when L > 1),
+// 32/L rows per pass.  Fixed policies cut each member's rows into contiguous
+// ranges.  The adaptive policy bins rows by exact length (a counting sort), so
+// that the 32 rows of a warp pass have equal length and no lane idles on the
+// FP64 pipe; rows up to 32 entries get one lane, longer rows about 32 entries
+// per lane; inside a member, longer rows come first.  Items keep member order,
+// which keeps the B blocks being gathered resident in L2.  No CTA ever waits
+// for another.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "batch_kernel.cuh"
+
+namespace spmv {
+
+static int policy_lanes(int policy) {
+  switch (policy) {
+    case SPMV_BATCH_L1: return 1;
+    case SPMV_BATCH_L2: return 2;
+    case SPMV_BATCH_L4: return 4;
+    case SPMV_BATCH_L8: return 8;
+    case SPMV_BATCH_L32: return 32;
+    default: return 0;  // adaptive
+  }
+}
+
+// Lanes for a row of `len` entries under the adaptive policy: at most about 32
+// entries per lane (fewer lanes keep the shuffle adds on the FP64 pipe few).
+static int adaptive_lanes(int64_t len) {
+  int L = 1;
+  while (L < 32 && (int64_t)L * 32 < len) L <<= 1;
+  return L;
+}
+
+// Items of about item_nnz work units (a row counts max(len, 1)) and at most
+// 64 warp passes.  Contiguous rows [p0, p1) (mode 0), or positions [p0, p1) of
+// the row list, all of length len (mode 1).
+static void cut_items(const int32_t* rp, int64_t p0, int64_t p1, int mat, int L, int mode, int64_t len,
+                      int item_nnz, std::vector<BatchItem>& out) {
+  const int64_t rows_cap = (int64_t)(32 / L) * 64;
+  int64_t s = p0, work = 0;
+  for (int64_t p = p0; p < p1; ++p) {
+    if (p > s && (work >= item_nnz || p - s >= rows_cap)) {
+      out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p, (int32_t)len, (int16_t)L, (int16_t)mode, 0});
+      s = p;
+      work = 0;
+    }
+    work += mode == 1 ? std::max<int64_t>(len, 1) : (mode == 2 ? len : std::max<int64_t>(rp[p + 1] - rp[p], 1));
+  }
+  if (p1 > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p1, (int32_t)len, (int16_t)L, (int16_t)mode, 0});
+}
+
+void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, int item_nnz,
+                       std::vector<BatchItem>& out, std::vector<int2>& rowlist) {
+  const int fixed = policy_lanes(policy);
+  if (fixed) {
+    cut_items(rp, 0, n_rows, mat, fixed, 0, 0, item_nnz, out);
+    return;
+  }
+  // counting sort of the rows by descending length (ascending row inside a length)
+  int64_t maxlen = 0;
+  for (int64_t r = 0; r < n_rows; ++r) maxlen = std::max<int64_t>(maxlen, rp[r + 1] - rp[r]);
+  std::vector<int64_t> start((size_t)maxlen + 2, 0);
+  for (int64_t r = 0; r < n_rows; ++r) start[(size_t)(maxlen - (rp[r + 1] - rp[r])) + 1]++;
+  for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+  const int64_t base = (int64_t)rowlist.size();
+  rowlist.resize((size_t)(base + n_rows));
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    rowlist[(size_t)(base + fill[(size_t)(maxlen - len)]++)] = make_int2((int)r, (int)rp[r]);
+  }
+  // rows of up to 32 entries: one item family per exact length (one lane per
+  // row, no divergence); longer rows: one family per lane count, lengths within
+  // a factor of two of each other (few rows per length, which would leave
+  // most lanes of a pass idle)
+  int64_t d = 0;
+  while (d <= maxlen) {
+    const int64_t len = maxlen - d;
+    const int L = adaptive_lanes(len);
+    int64_t e = d + 1;
+    if (len > 32)
+      while (e <= maxlen && adaptive_lanes(maxlen - e) == L && maxlen - e > 32) ++e;
+    const int64_t p0 = start[(size_t)d], p1 = start[(size_t)e];
+    if (p1 > p0) cut_items(rp, base + p0, base + p1, mat, L, len > 32 ? 2 : 1, len, item_nnz, out);
+    d = e;
+  }
+}
+
+}  // namespace spmv
+
+using namespace spmv;
+
+struct spmv_batch_plan {
+  int device = 0;
+  int num_sms = 0;
+  int k = 1;
+  std::vector<spmv_handle> plans;
+  std::vector<int32_t> policies;
+  spmv_batch_config cfg{};
+  std::vector<BatchMat> h_mats;
+  BatchMat* d_mats = nullptr;
+  BatchItem* d_items = nullptr;
+  int2* d_rowlist = nullptr;
+  int64_t n_items = 0;
+  int* d_counter = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool io_set = false;
+  bool vec = false;  // 16-byte loads/stores of right-hand-side rows
+};
+
+static void free_graph(spmv_batch_plan* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Graph of one batched product: counter reset + persistent kernel.
+static spmv_status build_graph(spmv_batch_plan* b) {
+  free_graph(b);
+  const void* kern = batch_kernel(b->k, b->vec);
+  int grid = b->num_sms * b->cfg.ctas_per_sm;
+  int dynamic = b->cfg.schedule ? 1 : 0;
+  int n_items = (int)b->n_items;
+  int k = b->k;
+  void* args[] = {(void*)&b->d_mats,    (void*)&b->d_items, (void*)&n_items, (void*)&b->d_rowlist,
+                  (void*)&b->d_counter, (void*)&dynamic,    (void*)&k};
+  SPMV_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
+  cudaError_t e2 = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, 0, b->cap_stream);
+  cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
+  if (e1 != cudaSuccess) return cuda_fail(e1, "graph memset node");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "graph kernel node");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamEndCapture");
+  SPMV_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return SPMV_OK;
+}
+
+// (Re)build the work list and the graph.
+static spmv_status rebuild(spmv_batch_plan* b) {
+  std::vector<BatchItem> items;
+  std::vector<int2> rowlist;
+  for (size_t m = 0; m < b->plans.size(); ++m)
+    build_batch_items(plan_host_row_ptr(b->plans[m]), plan_csr(b->plans[m])->n_rows, (int)m, b->policies[m],
+                      b->cfg.item_nnz, items, rowlist);
+  if (items.size() > (size_t)INT32_MAX || rowlist.size() > (size_t)INT32_MAX)
+    return fail(SPMV_ERR_ARG, "too many work items");
+  // Items stay in member order (inside a member, longest rows first): the warps
+  // in flight then work on a few neighbouring members whose B blocks fit in L2,
+  // instead of gathering at random from every member's B in DRAM.
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_rowlist) cudaFree(b->d_rowlist);
+  b->d_items = nullptr;
+  b->d_rowlist = nullptr;
+  b->n_items = (int64_t)items.size();
+  SPMV_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
+  if (!items.empty())
+    SPMV_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  SPMV_CUDA(cudaMalloc(&b->d_rowlist, sizeof(int2) * std::max<size_t>(rowlist.size(), 1)));
+  if (!rowlist.empty())
+    SPMV_CUDA(cudaMemcpy(b->d_rowlist, rowlist.data(), sizeof(int2) * rowlist.size(), cudaMemcpyHostToDevice));
+  return build_graph(b);
+}
+
+static spmv_status check_config(const spmv_batch_config* c) {
+  if (c->item_nnz < 64 || c->item_nnz > (1 << 20)) return fail(SPMV_ERR_ARG, "item_nnz out of range 64..2^20");
+  if (c->schedule != 0 && c->schedule != 1) return fail(SPMV_ERR_ARG, "schedule must be 0 or 1");
+  if (c->ctas_per_sm < 1 || c->ctas_per_sm > 8) return fail(SPMV_ERR_ARG, "ctas_per_sm out of range 1..8");
+  return SPMV_OK;
+}
+
+extern "C" {
+
+spmv_batch_config spmv_batch_default_config(void) {
+  spmv_batch_config c;
+  std::memset(&c, 0, sizeof(c));
+  c.item_nnz = 1024;
+  c.schedule = 1;
+  c.ctas_per_sm = 8;
+  return c;
+}
+
+spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_handle* plans, int32_t k,
+                              const int32_t* policies, const spmv_batch_config* cfg) {
+  if (!out) return fail(SPMV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !plans) return fail(SPMV_ERR_ARG, "count must be >= 1 with a plan array");
+  if (k < 1 || k > 16) return fail(SPMV_ERR_ARG, "k out of range 1..16");
+  spmv_batch_config c = cfg ? *cfg : spmv_batch_default_config();
+  spmv_status st = check_config(&c);
+  if (st != SPMV_OK) return st;
+  const int dev = plan_device(plans[0]);
+  for (int m = 0; m < count; ++m) {
+    if (!plans[m]) return fail(SPMV_ERR_ARG, "NULL plan in the batch");
+    if (plan_device(plans[m]) != dev) return fail(SPMV_ERR_ARG, "batch members on different devices");
+    if (policies && (policies[m] < 0 || policies[m] >= SPMV_BATCH_N_POLICIES))
+      return fail(SPMV_ERR_ARG, "unknown batch policy");
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != dev) SPMV_CUDA(cudaSetDevice(dev));
+  auto* b = new spmv_batch_plan();
+  b->device = dev;
+  b->k = k;
+  b->cfg = c;
+  b->plans.assign(plans, plans + count);
+  b->policies.assign(count, SPMV_BATCH_ADAPT);
+  if (policies) b->policies.assign(policies, policies + count);
+  auto bail = [&](spmv_status s) {
+    spmv_batch_destroy(b);
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    return s;
+  };
+  cudaError_t e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+  b->h_mats.resize(count);
+  for (int m = 0; m < count; ++m) {
+    const CsrDev* A = plan_csr(plans[m]);
+    b->h_mats[m] = BatchMat{A->row_ptr, A->col, A->val, nullptr, nullptr, k, k, A->n_rows};
+  }
+  e = cudaMalloc(&b->d_mats, sizeof(BatchMat) * count);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_mats, b->h_mats.data(), sizeof(BatchMat) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "batch allocation"));
+  st = rebuild(b);
+  if (st != SPMV_OK) return bail(st);
+  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  *out = b;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_set_io(spmv_batch_handle b, const double* const* B_ptrs, const int64_t* ldb,
+                              double* const* C_ptrs, const int64_t* ldc) {
+  if (!b || !B_ptrs || !C_ptrs) return fail(SPMV_ERR_ARG, "NULL argument");
+  for (size_t m = 0; m < b->h_mats.size(); ++m) {
+    const int64_t lb = ldb ? ldb[m] : b->k, lc = ldc ? ldc[m] : b->k;
+    if (lb < b->k || lc < b->k) return fail(SPMV_ERR_ARG, "ldb/ldc must be >= k");
+    if (!C_ptrs[m] && b->h_mats[m].n_rows > 0) return fail(SPMV_ERR_ARG, "NULL C pointer");
+  }
+  bool vec = (b->k % 2 == 0);
+  for (size_t m = 0; m < b->h_mats.size(); ++m) {
+    const int64_t lb = ldb ? ldb[m] : b->k, lc = ldc ? ldc[m] : b->k;
+    b->h_mats[m].B = B_ptrs[m];
+    b->h_mats[m].C = C_ptrs[m];
+    b->h_mats[m].ldb = lb;
+    b->h_mats[m].ldc = lc;
+    vec = vec && (lb % 2 == 0) && (lc % 2 == 0) && ((uintptr_t)B_ptrs[m] % 16 == 0) &&
+          ((uintptr_t)C_ptrs[m] % 16 == 0);
+  }
+  SPMV_CUDA(cudaMemcpy(b->d_mats, b->h_mats.data(), sizeof(BatchMat) * b->h_mats.size(), cudaMemcpyHostToDevice));
+  if (vec != b->vec || !b->exec) {
+    b->vec = vec;
+    spmv_status st = build_graph(b);
+    if (st != SPMV_OK) return st;
+  }
+  b->io_set = true;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream) {
+  if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
+  if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
+  SPMV_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream) {
+  if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
+  if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
+  for (size_t m = 0; m < b->plans.size(); ++m) {
+    const BatchMat& M = b->h_mats[m];
+    spmv_status st = spmv_apply_block(b->plans[m], M.B, b->k, M.ldb, M.C, M.ldc, stream);
+    if (st != SPMV_OK) return st;
+  }
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_set_config(spmv_batch_handle b, const spmv_batch_config* cfg) {
+  if (!b || !cfg) return fail(SPMV_ERR_ARG, "NULL argument");
+  spmv_status st = check_config(cfg);
+  if (st != SPMV_OK) return st;
+  b->cfg = *cfg;
+  return rebuild(b);
+}
+
+spmv_status spmv_batch_get_config(spmv_batch_handle b, spmv_batch_config* cfg) {
+  if (!b || !cfg) return fail(SPMV_ERR_ARG, "NULL argument");
+  *cfg = b->cfg;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_set_policies(spmv_batch_handle b, const int32_t* policies) {
+  if (!b || !policies) return fail(SPMV_ERR_ARG, "NULL argument");
+  for (size_t m = 0; m < b->plans.size(); ++m)
+    if (policies[m] < 0 || policies[m] >= SPMV_BATCH_N_POLICIES) return fail(SPMV_ERR_ARG, "unknown batch policy");
+  b->policies.assign(policies, policies + b->plans.size());
+  return rebuild(b);
+}
+
+spmv_status spmv_batch_autotune(spmv_batch_handle b, void* stream, int32_t reps, spmv_batch_config* best,
+                                float* times_ms) {
+  if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
+  if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
+  if (reps < 1) reps = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int item_opts[5] = {256, 512, 1024, 2048, 4096};
+  const int sched_opts[2] = {0, 1};
+  const int cta_opts[2] = {4, 8};
+  cudaEvent_t e0, e1;
+  SPMV_CUDA(cudaEventCreate(&e0));
+  SPMV_CUDA(cudaEventCreate(&e1));
+  spmv_batch_config keep = b->cfg, win = b->cfg;
+  float win_t = 1e30f;
+  int idx = 0;
+  spmv_status st = SPMV_OK;
+  std::vector<float> ts((size_t)reps);
+  for (int io = 0; io < 5 && st == SPMV_OK; ++io)
+    for (int so = 0; so < 2 && st == SPMV_OK; ++so)
+      for (int co = 0; co < 2 && st == SPMV_OK; ++co, ++idx) {
+        spmv_batch_config c = keep;
+        c.item_nnz = item_opts[io];
+        c.schedule = sched_opts[so];
+        c.ctas_per_sm = cta_opts[co];
+        b->cfg = c;
+        st = rebuild(b);
+        if (st != SPMV_OK) break;
+        cudaGraphLaunch(b->exec, s);  // warm-up
+        for (int r = 0; r < reps; ++r) {
+          cudaEventRecord(e0, s);
+          cudaGraphLaunch(b->exec, s);
+          cudaEventRecord(e1, s);
+          cudaError_t e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune timing");
+            break;
+          }
+          cudaEventElapsedTime(&ts[r], e0, e1);
+        }
+        if (st != SPMV_OK) break;
+        std::vector<float> sorted = ts;
+        std::sort(sorted.begin(), sorted.end());
+        const float med = sorted[sorted.size() / 2];
+        if (times_ms) times_ms[idx] = med;
+        if (med < win_t) {
+          win_t = med;
+          win = c;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->cfg = (st == SPMV_OK) ? win : keep;
+  spmv_status st2 = rebuild(b);
+  if (st != SPMV_OK) return st;
+  if (st2 != SPMV_OK) return st2;
+  if (best) *best = win;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_info(spmv_batch_handle b, int64_t* n_items, int64_t* total_rows, int64_t* total_nnz) {
+  if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
+  int64_t rows = 0, nnz = 0;
+  for (spmv_handle p : b->plans) {
+    rows += plan_csr(p)->n_rows;
+    nnz += plan_csr(p)->nnz;
+  }
+  if (n_items) *n_items = b->n_items;
+  if (total_rows) *total_rows = rows;
+  if (total_nnz) *total_nnz = nnz;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_destroy(spmv_batch_handle b) {
+  if (!b) return SPMV_OK;
+  cudaDeviceSynchronize();
+  free_graph(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_rowlist) cudaFree(b->d_rowlist);
+  if (b->d_mats) cudaFree(b->d_mats);
+  if (b->d_counter) cudaFree(b->d_counter);
+  delete b;
+  return SPMV_OK;
+}
+
+}  // extern "C"

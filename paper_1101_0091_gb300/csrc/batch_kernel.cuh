@@ -1,0 +1,170 @@
+// Device side of the batched product: member table, work items and the
+// persistent kernel (shared by the batch API and its allocation-free entry).
+#pragma once
+
+#include "device.cuh"
+
+namespace spmv {
+
+struct BatchMat {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const double* B;
+  double* C;
+  int64_t ldb, ldc;
+  int64_t n_rows;
+};
+
+// Work item.  mode 0: rows [p0, p1) of member `mat`, bounds from row_ptr.
+// mode 1: the rows listed at positions [p0, p1) of the (row, first entry)
+// list, all of length `len` (the length-binned rows of the adaptive policy).
+// mode 2: listed rows of unequal lengths (ends from row_ptr).
+// L lanes share one row; 32/L rows per warp pass.
+struct BatchItem {
+  int32_t mat, p0, p1, len;
+  int16_t lanes, mode;
+  int32_t pad;
+};
+
+// 16-byte loads of two consecutive right-hand-side values when B rows are
+// 16-byte aligned (VEC), else single 8-byte loads.
+template <int K, bool VEC>
+__device__ __forceinline__ void gather_row(const double* __restrict__ b, int k, double (&g)[K]) {
+  if (VEC && K >= 2) {
+#pragma unroll
+    for (int q = 0; q + 1 < K; q += 2) {
+      if (q < k) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(b + q));
+        g[q] = t.x;
+        g[q + 1] = t.y;
+      } else {
+        g[q] = 0.0;
+        g[q + 1] = 0.0;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) g[q] = (q < k) ? __ldg(b + q) : 0.0;
+  }
+}
+
+template <int L, int K, bool VEC>
+__device__ __forceinline__ void batch_rows(const BatchMat& M, const int2* __restrict__ rowlist,
+                                           const BatchItem& item, int k, int lane) {
+  constexpr int RPP = 32 / L;  // rows per warp pass
+  const int t = lane % L;
+  for (int base = item.p0; base < item.p1; base += RPP) {
+    const int i = base + lane / L;
+    const bool active = i < item.p1;
+    int r = 0, rs = 0, re = 0;
+    if (active) {
+      if (item.mode) {
+        const int2 e = __ldg(rowlist + i);
+        r = e.x;
+        rs = e.y;
+        re = item.mode == 1 ? rs + item.len : __ldg(M.row_ptr + r + 1);
+      } else {
+        r = i;
+        rs = __ldg(M.row_ptr + r);
+        re = __ldg(M.row_ptr + r + 1);
+      }
+    }
+    double acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = 0.0;
+    constexpr int NB = (L == 1 && K <= 2) ? 4 / K : 1;  // gathers issued before their FMAs
+    for (int j = rs + t; j < re; j += NB * L) {
+      double v[NB];
+      const double* b[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int jj = (j + u * L < re) ? j + u * L : j;
+        v[u] = ldcs(M.val + jj);
+        b[u] = M.B + (int64_t)ldcs(M.col + jj) * M.ldb;
+      }
+      double g[NB][K];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        if (j + u * L < re) {
+          gather_row<K, VEC>(b[u], k, g[u]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < K; ++q) g[u][q] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (j + u * L < re && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
+    }
+    if (L > 1) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc[q] = warp_sum_xor(acc[q], L);
+    }
+    if (active) {
+      double* out = M.C + (int64_t)r * M.ldc;
+      if (VEC && L == 1 && K >= 2) {
+#pragma unroll
+        for (int q = 0; q + 1 < K; q += 2)
+          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (q < k && (L == 1 || t == q % L)) out[q] = acc[q];
+      }
+    }
+  }
+}
+
+// Persistent kernel: warps take items round-robin (dynamic = 0) or from the
+// atomic counter (dynamic = 1, counter zeroed before the launch).
+template <int K, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
+            const int2* __restrict__ rowlist, int* __restrict__ counter, int dynamic, int k) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (kThreads / 32);
+  int it = wid;
+  if (dynamic) {
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+  }
+  while (it < n_items) {
+    const BatchItem item = items[it];
+    const BatchMat M = mats[item.mat];
+    switch (item.lanes) {
+      case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
+      case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
+      case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;
+      case 8: batch_rows<8, K, VEC>(M, rowlist, item, k, lane); break;
+      case 16: batch_rows<16, K, VEC>(M, rowlist, item, k, lane); break;
+      default: batch_rows<32, K, VEC>(M, rowlist, item, k, lane); break;
+    }
+    if (dynamic) {
+      if (lane == 0) it = atomicAdd(counter, 1);
+      it = __shfl_sync(0xffffffffu, it, 0);
+    } else {
+      it += nw;
+    }
+  }
+}
+
+template <bool VEC>
+static const void* batch_kernel_t(int k) {
+  if (k <= 1) return (const void*)k_batch<1, false>;
+  if (k <= 2) return (const void*)k_batch<2, VEC>;
+  if (k <= 4) return (const void*)k_batch<4, VEC>;
+  if (k <= 8) return (const void*)k_batch<8, VEC>;
+  return (const void*)k_batch<16, VEC>;
+}
+
+// The kernel for k right-hand sides; vec: every member's B and C rows are
+// 16-byte aligned and k is even (16-byte loads and stores).
+static inline const void* batch_kernel(int k, bool vec) {
+  return vec ? batch_kernel_t<true>(k) : batch_kernel_t<false>(k);
+}
+
+}  // namespace spmv

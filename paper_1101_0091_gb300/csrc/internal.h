@@ -103,6 +103,11 @@ struct HaloDev {
   bool val32_special = false;
 };
 
+// ------------------------------------------------------- plan accessors
+const CsrDev* plan_csr(spmv_handle h);              // device view of the whole matrix
+const int32_t* plan_host_row_ptr(spmv_handle h);    // host copy of row_ptr
+int plan_device(spmv_handle h);
+
 // ------------------------------------------------------- host builders
 bool validate_csr(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
                   std::string* why);

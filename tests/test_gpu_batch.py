@@ -1,0 +1,174 @@
+"""Batched persistent launch over many uneven matrices (graph replay), its
+policies, configurations and autotuner, against the oracle and against each
+member's own single-matrix kernels."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_util import TOL_FP64, dev, host
+
+pytestmark = pytest.mark.gpu
+
+K = 4
+
+
+def members(count=24, seed=0, integer=False):
+    out = []
+    for m in range(count):
+        A = gen.powerlaw_batch_member(m, seed=seed, dim_lo=1e3, dim_hi=2e4)
+        if integer:
+            A.val = np.random.default_rng(m).integers(-1024, 1025, A.nnz).astype(np.float64)
+        out.append(A)
+    return out
+
+
+def operands(As, k=K, integer=False, seed=1):
+    rng = np.random.default_rng(seed)
+    Bs = [(rng.integers(-1024, 1025, (A.n_cols, k)).astype(np.float64) if integer
+           else gen.rhs_block(A.n_cols, k, seed=100 + i)) for i, A in enumerate(As)]
+    return Bs
+
+
+def run_batch(lib, As, Bs, policies=None, k=K, cfg=None, separate=False):
+    import torch
+    plans = [lib.Plan.from_csr(A) for A in As]
+    Bd = [dev(B) for B in Bs]
+    Cd = [torch.full((A.n_rows, k), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+    with lib.Batch(plans, k, policies) as b:
+        if cfg:
+            b.set_config(**cfg)
+        b.set_io(Bd, Cd)
+        (b.apply_separate if separate else b.apply)()
+        torch.cuda.synchronize()
+        out = [host(C) for C in Cd]
+    for p in plans:
+        p.close()
+    return out
+
+
+def check(As, Bs, Cs, exact=False):
+    for A, B, C in zip(As, Bs, Cs):
+        ref = oracle.spmm(A, B)
+        if exact:
+            assert np.array_equal(C, ref)
+        else:
+            assert oracle.max_err_ratio(C, ref, oracle.abs_scale(A, B), TOL_FP64) <= 1.0
+
+
+@pytest.mark.parametrize("policy", ["l1", "l2", "l4", "l8", "l32", "adapt", "mixed"])
+def test_batch_matches_oracle(lib, policy):
+    As = members()
+    Bs = operands(As)
+    if policy == "mixed":
+        pol = [m % lib.SPMV_BATCH_N_POLICIES for m in range(len(As))]
+    else:
+        pol = [{v: k for k, v in lib.POLICY_NAMES.items()}[policy]] * len(As)
+    check(As, Bs, run_batch(lib, As, Bs, pol))
+
+
+def test_batch_integer_bit_exact(lib):
+    As = members(12, integer=True)
+    Bs = operands(As, integer=True)
+    pol = [m % lib.SPMV_BATCH_N_POLICIES for m in range(len(As))]
+    check(As, Bs, run_batch(lib, As, Bs, pol), exact=True)
+
+
+@pytest.mark.parametrize("policy,variant", [(0, 2), (1, 3), (2, 4), (3, 5), (4, 7)])
+def test_batch_equals_solo_kernel_bitwise(lib, policy, variant):
+    """A member under a fixed-L policy sums each row in the same order as the
+    single-matrix L-lanes kernel: the results agree bit for bit."""
+    import torch
+    As = members(6)
+    Bs = operands(As)
+    Cb = run_batch(lib, As, Bs, [policy] * len(As))
+    for A, B, C in zip(As, Bs, Cb):
+        with lib.Plan.from_csr(A, variant=variant) as p:
+            Cs = torch.empty((A.n_rows, K), dtype=torch.float64, device="cuda")
+            p.apply_block(dev(B), Cs)
+            assert np.array_equal(host(Cs), C)
+
+
+@pytest.mark.parametrize("cfg", [dict(item_nnz=64, schedule=0, ctas_per_sm=1),
+                                 dict(item_nnz=4096, schedule=1, ctas_per_sm=8),
+                                 dict(item_nnz=1 << 20, schedule=0, ctas_per_sm=4),
+                                 dict(item_nnz=300, schedule=1, ctas_per_sm=2)])
+def test_batch_configs_same_result(lib, cfg):
+    As = members(10)
+    Bs = operands(As)
+    pol = [lib.SPMV_BATCH_ADAPT] * len(As)
+    base = run_batch(lib, As, Bs, pol)
+    got = run_batch(lib, As, Bs, pol, cfg=cfg)
+    for a, b in zip(base, got):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_batch_other_k(lib, k):
+    As = members(8)
+    Bs = operands(As, k=k)
+    check(As, Bs, run_batch(lib, As, Bs, [lib.SPMV_BATCH_ADAPT] * len(As), k=k))
+
+
+def test_batch_separate_launches(lib):
+    As = members(8)
+    Bs = operands(As)
+    check(As, Bs, run_batch(lib, As, Bs, separate=True))
+
+
+def test_batch_replay_autotune_and_new_io(lib):
+    import torch
+    As = members(16)
+    Bs = operands(As)
+    plans = [lib.Plan.from_csr(A) for A in As]
+    Bd = [dev(B) for B in Bs]
+    Cd = [torch.zeros((A.n_rows, K), dtype=torch.float64, device="cuda") for A in As]
+    with lib.Batch(plans, K) as b:
+        n_items, rows, nnz = b.info()
+        assert rows == sum(A.n_rows for A in As) and nnz == sum(A.nnz for A in As) and n_items > len(As)
+        b.set_io(Bd, Cd)
+        for _ in range(3):
+            b.apply()
+        torch.cuda.synchronize()
+        first = [host(C) for C in Cd]
+        check(As, Bs, first)
+        best, times = b.autotune(reps=2)
+        assert len(times) == len(lib.AUTOTUNE_GRID) and np.all(times > 0)
+        c = b.config()
+        assert (c.item_nnz, c.schedule, c.ctas_per_sm) == (best.item_nnz, best.schedule, best.ctas_per_sm)
+        Cd2 = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+        b.set_io(Bd, Cd2)
+        b.apply()
+        torch.cuda.synchronize()
+        for a, C in zip(first, Cd2):
+            assert np.array_equal(a, host(C))
+    for p in plans:
+        p.close()
+
+
+def test_batch_empty_members_and_errors(lib):
+    import torch
+    empty = gen.CSR(0, 10, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    blank = gen.CSR(50, 10, np.zeros(51, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    A = gen.powerlaw(3000, seed=2)
+    As = [empty, blank, A]
+    Bs = [gen.rhs_block(M.n_cols, K, seed=i) for i, M in enumerate(As)]
+    Cs = run_batch(lib, As, Bs, [lib.SPMV_BATCH_ADAPT, lib.SPMV_BATCH_L1, lib.SPMV_BATCH_L32])
+    assert Cs[0].shape == (0, K)
+    assert np.array_equal(Cs[1], np.zeros((50, K)))
+    check([A], [Bs[2]], [Cs[2]])
+    with lib.Plan.from_csr(A) as p:
+        for bad in (dict(k=0), dict(k=17), dict(k=4, policies=[9])):
+            with pytest.raises(lib.SpmvError) as e:
+                lib.Batch([p], bad["k"], bad.get("policies"))
+            assert e.value.status == 1
+        with lib.Batch([p], 4) as b:
+            with pytest.raises(lib.SpmvError):
+                b.apply()        # no operands set
+            with pytest.raises(lib.SpmvError):
+                b.set_config(item_nnz=1)
+            with pytest.raises(lib.SpmvError):
+                b.set_config(schedule=2)
+            with pytest.raises(lib.SpmvError):
+                b.set_io([dev(np.zeros((A.n_cols, 4)))], [torch.zeros((A.n_rows, 2), dtype=torch.float64,
+                                                                        device="cuda")])
