@@ -251,6 +251,39 @@ spmv_status spmv_batch_info(spmv_batch_handle b, int64_t* n_items, int64_t* tota
 
 spmv_status spmv_batch_destroy(spmv_batch_handle b);
 
+/* Batched products without any device allocation.  The paper has no
+ * counterpart: this entry exists for callers that may not call cudaMalloc
+ * themselves or through a library -- applications that hand every byte of
+ * device memory to their own pool under a fixed budget, and latency-critical
+ * paths where an allocation's implicit device synchronisation and unbounded
+ * cost are not acceptable.  Such callers cannot create plans (plan creation
+ * allocates), so they pass their own device CRS arrays.
+ *
+ * Computes, for each member m < count, C_dev[m][i*ldc[m] + c] = sum over
+ * j = row_ptr_dev[m][i] .. row_ptr_dev[m][i+1]-1 of
+ * val_dev[m][j] * B_dev[m][col_dev[m][j]*ldb[m] + c], c < k (1 <= k <= 16),
+ * with lanes[m] lanes per row (1, 2, 4, 8, 16 or 32; NULL: 1) in one launch of
+ * the persistent batch kernel (atomic work counter).  All per-member arrays
+ * are HOST arrays of `count` entries; the pointers in them are DEVICE pointers
+ * of the current device; ldb/ldc NULL means k.  Results are the same as
+ * spmv_batch_apply with the matching fixed policy.
+ *
+ * Scratch: one static 8 MiB device array per device that loads the library,
+ * held until the process exits, holding the work counter, the member table and
+ * the work list.  Limits: count <= 8192 members and at most 327,669 work
+ * items (one item per 32 warp passes: 1024 rows at 1 lane per row), beyond
+ * which the call returns SPMV_ERR_ARG without touching the device.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call clears the
+ * counter and overwrites the table and the list in the shared array, so calls
+ * that overlap on the GPU (other streams, other host threads) race: order them
+ * on one stream.  Host calls are serialised by a mutex.  Asynchronous on
+ * `stream`; calls no cudaMalloc, cudaFree or allocating library routine. */
+spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_rows, const int32_t* const* row_ptr_dev,
+                                     const int32_t* const* col_dev, const double* const* val_dev,
+                                     const double* const* B_dev, const int64_t* ldb, double* const* C_dev,
+                                     const int64_t* ldc, int32_t k, const int32_t* lanes, void* stream);
+
 /* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).
  * out[34] (float64) for HOST CRS arrays and k right-hand sides:

@@ -176,3 +176,22 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+_SIGS["spmv_batch_apply_noalloc"] = ([_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp], ctypes.c_int)
+
+
+def spmv_batch_apply_noalloc(n_rows, row_ptr_dev, col_dev, val_dev, B_dev, ldb, C_dev, ldc, k: int,
+                             lanes=None, stream: int = 0) -> None:
+    """Per-member lists (host side) of row counts and DEVICE pointers; marshalled into host arrays."""
+    n = len(n_rows)
+    rows = np.ascontiguousarray(n_rows, dtype=np.int64)
+    ptrs = [(ctypes.c_void_p * n)(*p) for p in (row_ptr_dev, col_dev, val_dev, B_dev, C_dev)]
+    lb = np.ascontiguousarray(ldb, dtype=np.int64) if ldb is not None else None
+    lc = np.ascontiguousarray(ldc, dtype=np.int64) if ldc is not None else None
+    ln = np.ascontiguousarray(lanes, dtype=np.int32) if lanes is not None else None
+    c = lambda a: ctypes.cast(a, ctypes.c_void_p)  # noqa: E731
+    _check(_lib().spmv_batch_apply_noalloc(
+        n, rows.ctypes.data, c(ptrs[0]), c(ptrs[1]), c(ptrs[2]), c(ptrs[3]),
+        lb.ctypes.data if lb is not None else None, c(ptrs[4]), lc.ctypes.data if lc is not None else None, k,
+        ln.ctypes.data if ln is not None else None, stream))
