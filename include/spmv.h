@@ -285,6 +285,50 @@ spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_rows, const
                                      const int64_t* ldc, int32_t k, const int32_t* lanes, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * Cost model: an MLP predicting the log run time of each kernel variant from a
+ * matrix's features (spmv_features), so that a plan or batch member runs the
+ * variant with the smallest prediction.  The paper has no learned component
+ * (its Sec. 1.2 model is analytic); the network and its training are
+ * hand-written FP32 CUDA kernels:
+ *   Xn = (X - mean) * inv_std; H1 = relu(Xn W1^T + b1); H2 = relu(H1 W2^T + b2);
+ *   Y = H2 W3^T + b3; loss = sum(mask (Y - T)^2) / sum(mask); Adam updates.
+ * Parameters (host and device layout, float32): W1[H*F], b1[H], W2[H*H], b2[H],
+ * W3[V*H], b3[V].  X (M x F), T and mask (M x V) are row-major float32 DEVICE
+ * arrays; masked-out targets may hold any value.  All reductions run in a
+ * fixed order: results are deterministic.
+ * ------------------------------------------------------------------------- */
+spmv_status spmv_model_create(spmv_model_handle* out, int32_t n_in, int32_t n_hidden, int32_t n_out,
+                              const float* params /* host */);
+spmv_status spmv_model_info(spmv_model_handle m, int32_t* n_in, int32_t* n_hidden, int32_t* n_out,
+                            int64_t* n_params, int32_t* adam_steps);
+/* Replace the parameters (host array) and reset the Adam moments and step. */
+spmv_status spmv_model_set_params(spmv_model_handle m, const float* params);
+spmv_status spmv_model_get_params(spmv_model_handle m, float* params);
+/* Feature normalisation (host arrays of n_in), applied inside the forward pass. */
+spmv_status spmv_model_set_normalizer(spmv_model_handle m, const float* mean, const float* inv_std);
+/* Y_dev (M x n_out) = network(X_dev); asynchronous on stream. */
+spmv_status spmv_model_forward(spmv_model_handle m, const float* X_dev, int32_t M, float* Y_dev, void* stream);
+/* Forward + backward: loss (1 float, device; NULL: internal) and the gradient
+ * in the parameter layout (device; NULL: the model's own gradient buffer). */
+spmv_status spmv_model_loss_grad(spmv_model_handle m, const float* X_dev, const float* T_dev, const float* mask_dev,
+                                 int32_t M, float* loss_dev, float* grad_dev, void* stream);
+/* One Adam step with the given gradient (NULL: the model's own buffer). */
+spmv_status spmv_model_adam_step(spmv_model_handle m, const float* grad_dev, float lr, float beta1, float beta2,
+                                 float eps, void* stream);
+/* loss_grad + Adam (beta1 0.9, beta2 0.999, eps 1e-8). */
+spmv_status spmv_model_train_step(spmv_model_handle m, const float* X_dev, const float* T_dev, const float* mask_dev,
+                                  int32_t M, float lr, float* loss_dev, void* stream);
+/* Predict for M HOST feature rows (float64, M x n_in) and return, per row, the
+ * index of the smallest predicted log time (host int32[M]); predicted (host
+ * float32[M x n_out]) may be NULL.  Synchronises the stream. */
+spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32_t M, int32_t* choice,
+                              float* predicted, void* stream);
+/* Checkpoint with the normaliser, parameters and Adam state (binary file). */
+spmv_status spmv_model_save(spmv_model_handle m, const char* path);
+spmv_status spmv_model_load(spmv_model_handle* out, const char* path);
+spmv_status spmv_model_destroy(spmv_model_handle m);
+
+/* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).
  * out[34] (float64) for HOST CRS arrays and k right-hand sides:
  *   [0:13]  fraction of rows in length bin b: b(L) = 0 for L = 0, else

@@ -1,0 +1,49 @@
+"""The learned variant selector: trained by the library's own kernels on timed
+sweeps of generated matrices (seeds >= 1000), evaluated on held-out matrices
+(other seeds) against the exhaustive sweep, and compared with the method
+without it (every product on the default CRS_L1 kernel)."""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained(lib):
+    import torch
+    from paper_1101_0091_gb300 import selector
+    stream = torch.cuda.Stream()
+    train = selector.build_dataset(selector.training_matrices(100, seed=1000, scale=0.25), "plan", stream)
+    cm = selector.CostModel(len(selector.PLAN_VARIANTS), hidden=64, seed=0)
+    curve = cm.fit(train, epochs=1500, lr=3e-3)
+    return selector, cm, stream, train, curve
+
+
+def test_training_converges(trained):
+    selector, cm, stream, train, curve = trained
+    assert curve[-1] < 0.5 * curve[0]
+    choice, _ = cm.select(train.X)
+    r = selector.regret(train.times, choice)
+    assert r["total"] < 0.15, r
+
+
+def test_selector_gains_over_default_on_held_out(trained):
+    selector, cm, stream, train, curve = trained
+    held = [gen.eigen_shaped(400_000, seed=7, window=1 << 18),        # scattered rows of varying length
+            gen.powerlaw(200_000, seed=8, lmax=2000),                 # long power-law rows
+            gen.poisson3d_var(60, seed=9),                            # 7-point stencil
+            gen.powerlaw(150_000, lmin=40, lmax=40, seed=10)]         # constant long rows
+    test = selector.build_dataset(held, "plan", stream)
+    choice, _ = cm.select(test.X)
+    learned = selector.regret(test.times, choice)
+    default = selector.fixed_choice_regret(test.times, selector.PLAN_DEFAULT)
+    t_learned = test.times[np.arange(len(held)), choice].sum()
+    t_default = test.times[:, selector.PLAN_DEFAULT].sum()
+    names = [v[0] for v in selector.PLAN_VARIANTS]
+    print("held-out: chosen", [names[c] for c in choice], "best", [names[c] for c in test.times.argmin(axis=1)])
+    print("held-out regret learned", learned, "default", default, "time ratio", t_learned / t_default)
+    assert t_learned < 0.8 * t_default           # the network's gain over CRS_L1 everywhere
+    assert learned["total"] < default["total"]
+    assert learned["total"] < 0.5
