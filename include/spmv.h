@@ -194,9 +194,12 @@ typedef enum {
   SPMV_BATCH_L4 = 2,
   SPMV_BATCH_L8 = 3,
   SPMV_BATCH_L32 = 4,     /* a warp per row                                          */
-  SPMV_BATCH_ADAPT = 5,   /* per row: L = smallest power of two >= len/4, at most 32; */
-                          /* consecutive rows of equal L share an item               */
-  SPMV_BATCH_N_POLICIES = 6
+  SPMV_BATCH_ADAPT = 5,   /* rows binned by exact length (<= 32: one lane per row),   */
+                          /* longer rows with about 32 entries per lane (L <= 32)     */
+  SPMV_BATCH_SORTED = 6,  /* rows of <= 32 entries copied into a length-sorted       */
+                          /* SELL-32 layout (coalesced, one lane per row); longer     */
+                          /* rows as in ADAPT.  Costs a copy of those rows' entries.  */
+  SPMV_BATCH_N_POLICIES = 7
 } spmv_batch_policy;
 
 typedef struct {
@@ -210,7 +213,7 @@ typedef struct {
 spmv_batch_config spmv_batch_default_config(void);
 
 /* Build a batch over `count` plans (same device) with k right-hand sides each
- * (1 <= k <= 16).  policies[count] (NULL: all ADAPT) picks each member's row
+ * (1 <= k <= 16).  policies[count] (NULL: all SORTED) picks each member's row
  * policy.  Uploads the work list and the member table; no product runs. */
 spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_handle* plans, int32_t k,
                               const int32_t* policies, const spmv_batch_config* cfg);

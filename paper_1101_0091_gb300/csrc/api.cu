@@ -119,6 +119,8 @@ static void apply_tuning(spmv_plan* p) {
 namespace spmv {
 const CsrDev* plan_csr(spmv_handle h) { return &h->A; }
 const int32_t* plan_host_row_ptr(spmv_handle h) { return h->host.row_ptr.data(); }
+const int32_t* plan_host_col(spmv_handle h) { return h->host.col.data(); }
+const double* plan_host_val(spmv_handle h) { return h->host.val.data(); }
 int plan_device(spmv_handle h) { return h->device; }
 }  // namespace spmv
 

@@ -58,6 +58,73 @@ static void cut_items(const int32_t* rp, int64_t p0, int64_t p1, int mat, int L,
   if (p1 > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p1, (int32_t)len, (int16_t)L, (int16_t)mode, 0});
 }
 
+// Length-sorted SELL-32 copy of the rows with at most 32 entries (sorted
+// policy), appended for one member: rows by descending length (stable), 32 per
+// chunk, chunk length = its first (longest) row, column-major slots, padding
+// val +0.0 with the row's last column (0 for empty and padding rows).
+struct SortedSell {
+  std::vector<int64_t> chunk_ptr{0};
+  std::vector<int32_t> chunk_len, perm, col;
+  std::vector<double> val;
+};
+
+static void append_sorted_sell(const int32_t* rp, const int32_t* col, const double* val, int64_t n_rows,
+                               SortedSell& S, int64_t* first_chunk, int64_t* n_chunks) {
+  int64_t cnt[34] = {0};
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    if (len <= 32) cnt[32 - len + 1]++;
+  }
+  for (int i = 1; i < 34; ++i) cnt[i] += cnt[i - 1];
+  const int64_t n_short = cnt[33];
+  std::vector<int32_t> order((size_t)n_short);
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    if (len <= 32) order[(size_t)cnt[32 - len]++] = (int32_t)r;
+  }
+  *first_chunk = (int64_t)S.chunk_len.size();
+  *n_chunks = (n_short + 31) / 32;
+  for (int64_t i = 0; i < n_short; i += 32) {
+    const int32_t clen = rp[order[i] + 1] - rp[order[i]];
+    const int64_t base = S.chunk_ptr.back();
+    S.col.resize((size_t)(base + 32 * clen), 0);
+    S.val.resize((size_t)(base + 32 * clen), 0.0);
+    for (int t = 0; t < 32; ++t) {
+      const int32_t r = (i + t < n_short) ? order[(size_t)(i + t)] : -1;
+      S.perm.push_back(r);
+      const int64_t len = r >= 0 ? rp[r + 1] - rp[r] : 0;
+      int32_t last = 0;
+      for (int64_t j = 0; j < clen; ++j) {
+        const int64_t slot = base + j * 32 + t;
+        if (j < len) {
+          last = col[rp[r] + j];
+          S.col[(size_t)slot] = last;
+          S.val[(size_t)slot] = val[rp[r] + j];
+        } else {
+          S.col[(size_t)slot] = last;
+        }
+      }
+    }
+    S.chunk_len.push_back(clen);
+    S.chunk_ptr.push_back(base + 32 * (int64_t)clen);
+  }
+}
+
+// Items over chunks [c0, c0 + nc) of the sorted copy, about item_nnz slots each.
+static void cut_chunk_items(const SortedSell& S, int64_t c0, int64_t nc, int mat, int item_nnz,
+                            std::vector<BatchItem>& out) {
+  int64_t s = c0, work = 0;
+  for (int64_t c = c0; c < c0 + nc; ++c) {
+    if (c > s && work >= item_nnz) {
+      out.push_back(BatchItem{mat, (int32_t)s, (int32_t)c, 0, (int16_t)1, (int16_t)3, 0});
+      s = c;
+      work = 0;
+    }
+    work += std::max<int64_t>(32 * (int64_t)S.chunk_len[(size_t)c], 32);
+  }
+  if (c0 + nc > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)(c0 + nc), 0, (int16_t)1, (int16_t)3, 0});
+}
+
 void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, int item_nnz,
                        std::vector<BatchItem>& out, std::vector<int2>& rowlist) {
   const int fixed = policy_lanes(policy);
@@ -65,6 +132,7 @@ void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, i
     cut_items(rp, 0, n_rows, mat, fixed, 0, 0, item_nnz, out);
     return;
   }
+  const bool long_only = policy == SPMV_BATCH_SORTED;  // short rows live in the sorted SELL copy
   // counting sort of the rows by descending length (ascending row inside a length)
   int64_t maxlen = 0;
   for (int64_t r = 0; r < n_rows; ++r) maxlen = std::max<int64_t>(maxlen, rp[r + 1] - rp[r]);
@@ -90,7 +158,8 @@ void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, i
     if (len > 32)
       while (e <= maxlen && adaptive_lanes(maxlen - e) == L && maxlen - e > 32) ++e;
     const int64_t p0 = start[(size_t)d], p1 = start[(size_t)e];
-    if (p1 > p0) cut_items(rp, base + p0, base + p1, mat, L, len > 32 ? 2 : 1, len, item_nnz, out);
+    if (p1 > p0 && !(long_only && len <= 32))
+      cut_items(rp, base + p0, base + p1, mat, L, len > 32 ? 2 : 1, len, item_nnz, out);
     d = e;
   }
 }
@@ -117,7 +186,55 @@ struct spmv_batch_plan {
   cudaGraphExec_t exec = nullptr;
   bool io_set = false;
   bool vec = false;  // 16-byte loads/stores of right-hand-side rows
+  // length-sorted SELL copy of the sorted-policy members (rebuilt when the policies change)
+  std::vector<int32_t> sell_policies;
+  SortedSell sell_host;
+  std::vector<int64_t> sell_first, sell_count;
+  BatchSell sell{};
+  std::vector<void*> sell_ptrs;
 };
+
+static void free_sell(spmv_batch_plan* b) {
+  for (void* p : b->sell_ptrs) cudaFree(p);
+  b->sell_ptrs.clear();
+  b->sell = BatchSell{};
+}
+
+// Build (when the policies changed) and upload the sorted SELL copy.
+static spmv_status ensure_sell(spmv_batch_plan* b) {
+  if (b->sell_policies == b->policies && (b->sell.perm || b->sell_host.chunk_len.empty())) return SPMV_OK;
+  free_sell(b);
+  b->sell_host = SortedSell{};
+  const size_t n = b->plans.size();
+  b->sell_first.assign(n, 0);
+  b->sell_count.assign(n, 0);
+  for (size_t m = 0; m < n; ++m)
+    if (b->policies[m] == SPMV_BATCH_SORTED)
+      append_sorted_sell(plan_host_row_ptr(b->plans[m]), plan_host_col(b->plans[m]), plan_host_val(b->plans[m]),
+                         plan_csr(b->plans[m])->n_rows, b->sell_host, &b->sell_first[m], &b->sell_count[m]);
+  b->sell_policies = b->policies;
+  const SortedSell& S = b->sell_host;
+  if (S.chunk_len.empty()) return SPMV_OK;
+  auto up = [&](const void* src, size_t bytes, void** dst) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    b->sell_ptrs.push_back(*dst);
+    return bytes ? cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  void *cp, *cl, *pm, *co, *va;
+  SPMV_CUDA(up(S.chunk_ptr.data(), sizeof(int64_t) * S.chunk_ptr.size(), &cp));
+  SPMV_CUDA(up(S.chunk_len.data(), sizeof(int32_t) * S.chunk_len.size(), &cl));
+  SPMV_CUDA(up(S.perm.data(), sizeof(int32_t) * S.perm.size(), &pm));
+  SPMV_CUDA(up(S.col.data(), sizeof(int32_t) * S.col.size(), &co));
+  SPMV_CUDA(up(S.val.data(), sizeof(double) * S.val.size(), &va));
+  b->sell = BatchSell{(const int64_t*)cp, (const int32_t*)cl, (const int32_t*)pm, (const int32_t*)co,
+                      (const double*)va};
+  // the entries now live on the device; keep the chunk lengths for cutting items
+  std::vector<int32_t>().swap(b->sell_host.col);
+  std::vector<double>().swap(b->sell_host.val);
+  std::vector<int32_t>().swap(b->sell_host.perm);
+  return SPMV_OK;
+}
 
 static void free_graph(spmv_batch_plan* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -134,8 +251,8 @@ static spmv_status build_graph(spmv_batch_plan* b) {
   int dynamic = b->cfg.schedule ? 1 : 0;
   int n_items = (int)b->n_items;
   int k = b->k;
-  void* args[] = {(void*)&b->d_mats,    (void*)&b->d_items, (void*)&n_items, (void*)&b->d_rowlist,
-                  (void*)&b->d_counter, (void*)&dynamic,    (void*)&k};
+  void* args[] = {(void*)&b->d_mats, (void*)&b->d_items,   (void*)&n_items, (void*)&b->d_rowlist,
+                  (void*)&b->sell,   (void*)&b->d_counter, (void*)&dynamic, (void*)&k};
   SPMV_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
   cudaError_t e2 = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, 0, b->cap_stream);
@@ -149,11 +266,16 @@ static spmv_status build_graph(spmv_batch_plan* b) {
 
 // (Re)build the work list and the graph.
 static spmv_status rebuild(spmv_batch_plan* b) {
+  spmv_status st = ensure_sell(b);
+  if (st != SPMV_OK) return st;
   std::vector<BatchItem> items;
   std::vector<int2> rowlist;
-  for (size_t m = 0; m < b->plans.size(); ++m)
+  for (size_t m = 0; m < b->plans.size(); ++m) {
+    if (b->policies[m] == SPMV_BATCH_SORTED && b->sell_count[m] > 0)
+      cut_chunk_items(b->sell_host, b->sell_first[m], b->sell_count[m], (int)m, b->cfg.item_nnz, items);
     build_batch_items(plan_host_row_ptr(b->plans[m]), plan_csr(b->plans[m])->n_rows, (int)m, b->policies[m],
                       b->cfg.item_nnz, items, rowlist);
+  }
   if (items.size() > (size_t)INT32_MAX || rowlist.size() > (size_t)INT32_MAX)
     return fail(SPMV_ERR_ARG, "too many work items");
   // Items stay in member order (inside a member, longest rows first): the warps
@@ -215,7 +337,7 @@ spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_
   b->k = k;
   b->cfg = c;
   b->plans.assign(plans, plans + count);
-  b->policies.assign(count, SPMV_BATCH_ADAPT);
+  b->policies.assign(count, SPMV_BATCH_SORTED);
   if (policies) b->policies.assign(policies, policies + count);
   auto bail = [&](spmv_status s) {
     spmv_batch_destroy(b);
@@ -390,6 +512,7 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_rowlist) cudaFree(b->d_rowlist);
   if (b->d_mats) cudaFree(b->d_mats);
+  free_sell(b);
   if (b->d_counter) cudaFree(b->d_counter);
   delete b;
   return SPMV_OK;

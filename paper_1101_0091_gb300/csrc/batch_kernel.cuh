@@ -20,11 +20,24 @@ struct BatchMat {
 // mode 1: the rows listed at positions [p0, p1) of the (row, first entry)
 // list, all of length `len` (the length-binned rows of the adaptive policy).
 // mode 2: listed rows of unequal lengths (ends from row_ptr).
+// mode 3: chunks [p0, p1) of the length-sorted SELL-32 copy (sorted policy):
+// one lane per row, slots column-major inside a chunk.
 // L lanes share one row; 32/L rows per warp pass.
 struct BatchItem {
   int32_t mat, p0, p1, len;
   int16_t lanes, mode;
   int32_t pad;
+};
+
+// Length-sorted SELL-32 copy of the short rows of the members with the sorted
+// policy: chunk c holds 32 rows (row index perm[32c + t], -1 for padding) of
+// chunk_len[c] slots each at chunk_ptr[c] + 32 j + t.
+struct BatchSell {
+  const int64_t* chunk_ptr;
+  const int32_t* chunk_len;
+  const int32_t* perm;
+  const int32_t* col;
+  const double* val;
 };
 
 // 16-byte loads of two consecutive right-hand-side values when B rows are
@@ -118,12 +131,56 @@ __device__ __forceinline__ void batch_rows(const BatchMat& M, const int2* __rest
   }
 }
 
+template <int K, bool VEC>
+__device__ __forceinline__ void batch_chunks(const BatchMat& M, const BatchSell& S, const BatchItem& item, int k,
+                                             int lane) {
+  for (int c = item.p0; c < item.p1; ++c) {
+    const int len = __ldg(S.chunk_len + c);
+    const int64_t base = __ldg(S.chunk_ptr + c) + lane;
+    const int r = __ldg(S.perm + (int64_t)c * 32 + lane);
+    double acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = 0.0;
+    constexpr int NB = K <= 2 ? 4 / K : 1;  // gathers issued before their FMAs
+    for (int j = 0; j < len; j += NB) {
+      double v[NB];
+      const double* b[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int64_t slot = base + (int64_t)((j + u < len) ? j + u : j) * 32;
+        v[u] = ldcs(S.val + slot);
+        b[u] = M.B + (int64_t)ldcs(S.col + slot) * M.ldb;
+      }
+      double g[NB][K];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) gather_row<K, VEC>(b[u], k, g[u]);
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (j + u < len && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
+    }
+    if (r >= 0) {
+      double* out = M.C + (int64_t)r * M.ldc;
+      if (VEC && K >= 2) {
+#pragma unroll
+        for (int q = 0; q + 1 < K; q += 2)
+          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (q < k) out[q] = acc[q];
+      }
+    }
+  }
+}
+
 // Persistent kernel: warps take items round-robin (dynamic = 0) or from the
 // atomic counter (dynamic = 1, counter zeroed before the launch).
 template <int K, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
-            const int2* __restrict__ rowlist, int* __restrict__ counter, int dynamic, int k) {
+            const int2* __restrict__ rowlist, BatchSell sell, int* __restrict__ counter, int dynamic, int k) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (kThreads / 32);
@@ -135,7 +192,9 @@ __global__ void __launch_bounds__(kThreads)
   while (it < n_items) {
     const BatchItem item = items[it];
     const BatchMat M = mats[item.mat];
-    switch (item.lanes) {
+    if (item.mode == 3) {
+      batch_chunks<K, VEC>(M, sell, item, k, lane);
+    } else switch (item.lanes) {
       case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
       case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
       case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;

@@ -106,6 +106,8 @@ struct HaloDev {
 // ------------------------------------------------------- plan accessors
 const CsrDev* plan_csr(spmv_handle h);              // device view of the whole matrix
 const int32_t* plan_host_row_ptr(spmv_handle h);    // host copy of row_ptr
+const int32_t* plan_host_col(spmv_handle h);        // host copy of col_idx
+const double* plan_host_val(spmv_handle h);         // host copy of val
 int plan_device(spmv_handle h);
 
 // ------------------------------------------------------- host builders

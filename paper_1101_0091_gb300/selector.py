@@ -6,7 +6,7 @@ Two contexts share the code:
 * "plan":  single-matrix products, k = 1; the variants are the plan kernels
            (CRS_L1/L2/L4/L8/L32, CRS_STAGED, SELL-32 with sigma 1/256/4096).
 * "batch": members of a batched launch, k = 4; the variants are the batch row
-           policies (fixed 1/2/4/8/32 lanes per row, adaptive).
+           policies (fixed 1/2/4/8/32 lanes per row, adaptive, sorted).
 
 Targets are log(seconds); the network predicts one value per variant and the
 selection is the argmin.  Training matrices come from seeds >= 1000 of the
@@ -26,8 +26,8 @@ from . import _binding_model as bm
 PLAN_VARIANTS = [("crs_l1", 2, 1), ("crs_l2", 3, 1), ("crs_l4", 4, 1), ("crs_l8", 5, 1), ("crs_l32", 7, 1),
                  ("crs_staged", 1, 1), ("sell_s1", 8, 1), ("sell_s256", 8, 256), ("sell_s4096", 8, 4096)]
 PLAN_DEFAULT = 0          # CRS_L1, the plan's AUTO kernel
-BATCH_POLICIES = [("l1", 0), ("l2", 1), ("l4", 2), ("l8", 3), ("l32", 4), ("adapt", 5)]
-BATCH_DEFAULT = 5         # adaptive
+BATCH_POLICIES = [("l1", 0), ("l2", 1), ("l4", 2), ("l8", 3), ("l32", 4), ("adapt", 5), ("sorted", 6)]
+BATCH_DEFAULT = 6         # sorted, the batch's default policy
 N_FEATURES = 34
 
 

@@ -56,7 +56,7 @@ def check(As, Bs, Cs, exact=False):
             assert oracle.max_err_ratio(C, ref, oracle.abs_scale(A, B), TOL_FP64) <= 1.0
 
 
-@pytest.mark.parametrize("policy", ["l1", "l2", "l4", "l8", "l32", "adapt", "mixed"])
+@pytest.mark.parametrize("policy", ["l1", "l2", "l4", "l8", "l32", "adapt", "sorted", "mixed"])
 def test_batch_matches_oracle(lib, policy):
     As = members()
     Bs = operands(As)
@@ -96,11 +96,12 @@ def test_batch_equals_solo_kernel_bitwise(lib, policy, variant):
 def test_batch_configs_same_result(lib, cfg):
     As = members(10)
     Bs = operands(As)
-    pol = [lib.SPMV_BATCH_ADAPT] * len(As)
-    base = run_batch(lib, As, Bs, pol)
-    got = run_batch(lib, As, Bs, pol, cfg=cfg)
-    for a, b in zip(base, got):
-        assert np.array_equal(a, b)
+    for p in (lib.SPMV_BATCH_ADAPT, lib.SPMV_BATCH_SORTED):
+        pol = [p] * len(As)
+        base = run_batch(lib, As, Bs, pol)
+        got = run_batch(lib, As, Bs, pol, cfg=cfg)
+        for a, b in zip(base, got):
+            assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("k", [1, 3, 16])
