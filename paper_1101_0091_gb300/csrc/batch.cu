@@ -180,6 +180,7 @@ struct spmv_batch_plan {
   BatchItem* d_items = nullptr;
   int2* d_rowlist = nullptr;
   int64_t n_items = 0;
+  int64_t n_chunk_items = 0;  // sorted-chunk items in the list
   int* d_counter = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -243,19 +244,23 @@ static void free_graph(spmv_batch_plan* b) {
   b->graph = nullptr;
 }
 
-// Graph of one batched product: counter reset + persistent kernel.
+// Graph of one batched product: counter reset + persistent kernel (the
+// rows-only variant when the list holds no sorted chunks).
 static spmv_status build_graph(spmv_batch_plan* b) {
   free_graph(b);
-  const void* kern = batch_kernel(b->k, b->vec);
   int grid = b->num_sms * b->cfg.ctas_per_sm;
   int dynamic = b->cfg.schedule ? 1 : 0;
   int n_items = (int)b->n_items;
   int k = b->k;
-  void* args[] = {(void*)&b->d_mats, (void*)&b->d_items,   (void*)&n_items, (void*)&b->d_rowlist,
-                  (void*)&b->sell,   (void*)&b->d_counter, (void*)&dynamic, (void*)&k};
+  void* a_all[] = {(void*)&b->d_mats, (void*)&b->d_items,   (void*)&n_items, (void*)&b->d_rowlist,
+                   (void*)&b->sell,   (void*)&b->d_counter, (void*)&dynamic, (void*)&k};
+  void* a_rows[] = {(void*)&b->d_mats,    (void*)&b->d_items, (void*)&n_items, (void*)&b->d_rowlist,
+                    (void*)&b->d_counter, (void*)&dynamic,    (void*)&k};
+  const bool chunks = b->n_chunk_items > 0;
   SPMV_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
-  cudaError_t e2 = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, 0, b->cap_stream);
+  cudaError_t e2 = cudaLaunchKernel(chunks ? batch_kernel(b->k, b->vec) : batch_rows_kernel(b->k, b->vec),
+                                    dim3(grid), dim3(kThreads), chunks ? a_all : a_rows, 0, b->cap_stream);
   cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
   if (e1 != cudaSuccess) return cuda_fail(e1, "graph memset node");
   if (e2 != cudaSuccess) return cuda_fail(e2, "graph kernel node");
@@ -281,6 +286,7 @@ static spmv_status rebuild(spmv_batch_plan* b) {
   // Items stay in member order (inside a member, longest rows first): the warps
   // in flight then work on a few neighbouring members whose B blocks fit in L2,
   // instead of gathering at random from every member's B in DRAM.
+  b->n_chunk_items = std::count_if(items.begin(), items.end(), [](const BatchItem& it) { return it.mode == 3; });
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_rowlist) cudaFree(b->d_rowlist);
   b->d_items = nullptr;

@@ -132,8 +132,12 @@ __device__ __forceinline__ void batch_rows(const BatchMat& M, const int2* __rest
 }
 
 template <int K, bool VEC>
-__device__ __forceinline__ void batch_chunks(const BatchMat& M, const BatchSell& S, const BatchItem& item, int k,
-                                             int lane) {
+__device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, const BatchSell& S,
+                                             const BatchItem& item, int k, int lane) {
+  struct {
+    const double* B;
+    int64_t ldb;
+  } M = {Mp->B, Mp->ldb};  // only what the inner loop needs stays in registers
   for (int c = item.p0; c < item.p1; ++c) {
     const int len = __ldg(S.chunk_len + c);
     const int64_t base = __ldg(S.chunk_ptr + c) + lane;
@@ -161,7 +165,7 @@ __device__ __forceinline__ void batch_chunks(const BatchMat& M, const BatchSell&
           if (j + u < len && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
     }
     if (r >= 0) {
-      double* out = M.C + (int64_t)r * M.ldc;
+      double* out = Mp->C + (int64_t)r * Mp->ldc;
       if (VEC && K >= 2) {
 #pragma unroll
         for (int q = 0; q + 1 < K; q += 2)
@@ -177,24 +181,27 @@ __device__ __forceinline__ void batch_chunks(const BatchMat& M, const BatchSell&
 
 // Persistent kernel: warps take items round-robin (dynamic = 0) or from the
 // atomic counter (dynamic = 1, counter zeroed before the launch).
+// Next item index of the calling warp: round-robin or from the atomic counter.
+__device__ __forceinline__ int next_item(int it, int nw, int dynamic, int* counter, int lane) {
+  if (!dynamic) return it + nw;
+  int v = 0;
+  if (lane == 0) v = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Persistent kernel over row items (modes 0-2).
 template <int K, bool VEC>
 __global__ void __launch_bounds__(kThreads)
-    k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
-            const int2* __restrict__ rowlist, BatchSell sell, int* __restrict__ counter, int dynamic, int k) {
+    k_batch_rows(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
+                 const int2* __restrict__ rowlist, int* __restrict__ counter, int dynamic, int k) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (kThreads / 32);
-  int it = wid;
-  if (dynamic) {
-    if (lane == 0) it = atomicAdd(counter, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
-  }
+  int it = dynamic ? next_item(0, nw, 1, counter, lane) : wid;
   while (it < n_items) {
     const BatchItem item = items[it];
     const BatchMat M = mats[item.mat];
-    if (item.mode == 3) {
-      batch_chunks<K, VEC>(M, sell, item, k, lane);
-    } else switch (item.lanes) {
+    switch (item.lanes) {
       case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
       case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
       case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;
@@ -202,13 +209,48 @@ __global__ void __launch_bounds__(kThreads)
       case 16: batch_rows<16, K, VEC>(M, rowlist, item, k, lane); break;
       default: batch_rows<32, K, VEC>(M, rowlist, item, k, lane); break;
     }
-    if (dynamic) {
-      if (lane == 0) it = atomicAdd(counter, 1);
-      it = __shfl_sync(0xffffffffu, it, 0);
-    } else {
-      it += nw;
-    }
+    it = next_item(it, nw, dynamic, counter, lane);
   }
+}
+
+// Persistent kernel over all item modes.  Sorted-chunk items and row items of
+// one member stay next to each other in the list, so a member's B block is
+// gathered while it is resident in L2 (two separate kernels, one per mode,
+// would stream every B block twice).
+template <int K, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
+            const int2* __restrict__ rowlist, BatchSell sell, int* __restrict__ counter, int dynamic, int k) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (kThreads / 32);
+  int it = dynamic ? next_item(0, nw, 1, counter, lane) : wid;
+  while (it < n_items) {
+    const BatchItem item = items[it];
+    if (item.mode == 3) {
+      batch_chunks<K, VEC>(mats + item.mat, sell, item, k, lane);
+    } else {
+      const BatchMat M = mats[item.mat];
+      switch (item.lanes) {
+        case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
+        case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
+        case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;
+        case 8: batch_rows<8, K, VEC>(M, rowlist, item, k, lane); break;
+        case 16: batch_rows<16, K, VEC>(M, rowlist, item, k, lane); break;
+        default: batch_rows<32, K, VEC>(M, rowlist, item, k, lane); break;
+      }
+    }
+    it = next_item(it, nw, dynamic, counter, lane);
+  }
+}
+
+template <bool VEC>
+static const void* batch_rows_kernel_t(int k) {
+  if (k <= 1) return (const void*)k_batch_rows<1, false>;
+  if (k <= 2) return (const void*)k_batch_rows<2, VEC>;
+  if (k <= 4) return (const void*)k_batch_rows<4, VEC>;
+  if (k <= 8) return (const void*)k_batch_rows<8, VEC>;
+  return (const void*)k_batch_rows<16, VEC>;
 }
 
 template <bool VEC>
@@ -220,8 +262,12 @@ static const void* batch_kernel_t(int k) {
   return (const void*)k_batch<16, VEC>;
 }
 
-// The kernel for k right-hand sides; vec: every member's B and C rows are
-// 16-byte aligned and k is even (16-byte loads and stores).
+// The kernels for k right-hand sides; vec: every member's B and C rows are
+// 16-byte aligned and k is even (16-byte loads and stores).  The rows-only
+// variant serves work lists without sorted chunks.
+static inline const void* batch_rows_kernel(int k, bool vec) {
+  return vec ? batch_rows_kernel_t<true>(k) : batch_rows_kernel_t<false>(k);
+}
 static inline const void* batch_kernel(int k, bool vec) {
   return vec ? batch_kernel_t<true>(k) : batch_kernel_t<false>(k);
 }

@@ -106,10 +106,9 @@ extern "C" spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_
   const BatchItem* ditems = reinterpret_cast<const BatchItem*>(d + kNoAllocItemsOffset);
   const int2* rowlist = nullptr;
   int* counter = reinterpret_cast<int*>(d);
-  BatchSell no_sell{};  // contiguous row items only
   int ni = (int)n_items, dynamic = 1, kk = k;
-  void* args[] = {(void*)&mats,    (void*)&ditems,  (void*)&ni,      (void*)&rowlist,
-                  (void*)&no_sell, (void*)&counter, (void*)&dynamic, (void*)&kk};
-  SPMV_CUDA(cudaLaunchKernel(batch_kernel(k, vec), dim3(sms * 4), dim3(kThreads), args, 0, s));
+  void* args[] = {(void*)&mats, (void*)&ditems, (void*)&ni, (void*)&rowlist, (void*)&counter, (void*)&dynamic,
+                  (void*)&kk};
+  SPMV_CUDA(cudaLaunchKernel(batch_rows_kernel(k, vec), dim3(sms * 4), dim3(kThreads), args, 0, s));
   return SPMV_OK;
 }

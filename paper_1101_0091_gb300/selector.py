@@ -200,6 +200,36 @@ class CostModel:
             pass
 
 
+def batch_training_matrices(count: int, seed: int = 1000):
+    """Generated batch members (seeds >= 1000): members of the uneven-batch
+    generator itself (other seeds), power-law rows with varied exponents and
+    caps over log-uniform sizes, constant-length rows, stencils."""
+    import gen
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fam = i % 4
+        s = seed + i
+        n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
+        if fam == 0:
+            out.append(gen.powerlaw_batch_member(i, seed=s))
+        elif fam == 1:
+            out.append(gen.powerlaw(n, alpha=float(rng.uniform(1.6, 3.2)), lmax=int(rng.choice([8, 64, 512, 2000])),
+                                    seed=s))
+        elif fam == 2:
+            L = int(rng.choice([1, 2, 4, 8, 16, 40, 100]))
+            out.append(gen.powerlaw(n, lmin=L, lmax=min(L, n), seed=s))
+        else:
+            out.append(gen.poisson3d_var(int(rng.integers(10, 60)), seed=s))
+    return out
+
+
+def train_model(data: Dataset, n_variants: int, epochs: int = 2000, seed: int = 0) -> CostModel:
+    cm = CostModel(n_variants, hidden=64, seed=seed)
+    cm.fit(data, epochs=epochs)
+    return cm
+
+
 def regret(times: np.ndarray, choice: np.ndarray) -> dict:
     """Regret of a choice against the exhaustive sweep: sum(t_chosen)/sum(t_best) - 1
     and the mean of the per-matrix ratios minus one."""
