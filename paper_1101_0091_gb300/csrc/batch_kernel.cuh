@@ -63,8 +63,9 @@ __device__ __forceinline__ void gather_row(const double* __restrict__ b, int k, 
 }
 
 template <int L, int K, bool VEC>
-__device__ __forceinline__ void batch_rows(const BatchMat& M, const int2* __restrict__ rowlist,
+__device__ __forceinline__ void batch_rows(const BatchMat* __restrict__ Mp, const int2* __restrict__ rowlist,
                                            const BatchItem& item, int k, int lane) {
+  const BatchMat& M = *Mp;  // fields are read where used, not held across the item
   constexpr int RPP = 32 / L;  // rows per warp pass
   const int t = lane % L;
   for (int base = item.p0; base < item.p1; base += RPP) {
@@ -200,14 +201,13 @@ __global__ void __launch_bounds__(kThreads)
   int it = dynamic ? next_item(0, nw, 1, counter, lane) : wid;
   while (it < n_items) {
     const BatchItem item = items[it];
-    const BatchMat M = mats[item.mat];
     switch (item.lanes) {
-      case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
-      case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
-      case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;
-      case 8: batch_rows<8, K, VEC>(M, rowlist, item, k, lane); break;
-      case 16: batch_rows<16, K, VEC>(M, rowlist, item, k, lane); break;
-      default: batch_rows<32, K, VEC>(M, rowlist, item, k, lane); break;
+      case 1: batch_rows<1, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+      case 2: batch_rows<2, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+      case 4: batch_rows<4, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+      case 8: batch_rows<8, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+      case 16: batch_rows<16, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+      default: batch_rows<32, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
     }
     it = next_item(it, nw, dynamic, counter, lane);
   }
@@ -230,14 +230,13 @@ __global__ void __launch_bounds__(kThreads)
     if (item.mode == 3) {
       batch_chunks<K, VEC>(mats + item.mat, sell, item, k, lane);
     } else {
-      const BatchMat M = mats[item.mat];
       switch (item.lanes) {
-        case 1: batch_rows<1, K, VEC>(M, rowlist, item, k, lane); break;
-        case 2: batch_rows<2, K, VEC>(M, rowlist, item, k, lane); break;
-        case 4: batch_rows<4, K, VEC>(M, rowlist, item, k, lane); break;
-        case 8: batch_rows<8, K, VEC>(M, rowlist, item, k, lane); break;
-        case 16: batch_rows<16, K, VEC>(M, rowlist, item, k, lane); break;
-        default: batch_rows<32, K, VEC>(M, rowlist, item, k, lane); break;
+        case 1: batch_rows<1, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+        case 2: batch_rows<2, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+        case 4: batch_rows<4, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+        case 8: batch_rows<8, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+        case 16: batch_rows<16, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
+        default: batch_rows<32, K, VEC>(mats + item.mat, rowlist, item, k, lane); break;
       }
     }
     it = next_item(it, nw, dynamic, counter, lane);
