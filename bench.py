@@ -65,6 +65,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison of forms")
+    ap.add_argument("--selector", action="store_true",
+                    help="train the cost model on generated matrices (seeds >= 1000) and report its choice, "
+                         "its regret against the exhaustive sweep and its gain over the default")
+    ap.add_argument("--selector-train", type=int, default=100, help="training matrices for --selector")
+    ap.add_argument("--selector-stride", type=int, default=4,
+                    help="batch workload: sweep every n-th member exhaustively for the regret")
     return ap.parse_args()
 
 
@@ -315,25 +321,37 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         "wall_s_timed": round(r["wall_s"], 4),
     }
     if not args.no_e2e:
-        # through the C ABI from pinned host buffers: H2D of B and D2H of C inside the timed region
-        Bpin = torch.from_numpy(np.ascontiguousarray(Bh)).pin_memory()
-        Cpin = torch.empty(C.shape, dtype=torch.float64).pin_memory()
-        n_e2e = max(3, min(args.steps, 20))
-        for _ in range(2):
-            plan.apply_host_ptr(Bpin.data_ptr(), k, Cpin.data_ptr(), stream)
+        # through the C ABI from pinned host buffers: every step copies its B in (H2D) and its C out (D2H)
+        # inside the timed region.  Pipelined steps (spmv_apply_host_async: copy-in of step i+1 and
+        # copy-out of step i-1 overlap the product of step i), and one synchronous call per step.
+        Bpin = [torch.from_numpy(np.ascontiguousarray(Bh)).pin_memory() for _ in range(2)]
+        Cpin = [torch.empty(C.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+        n_e2e = max(3, min(args.steps, 40))
+        for i in range(4):
+            plan.apply_host_async(Bpin[i % 2], Cpin[i % 2], k, stream)
+        plan.host_sync()
         timer.barrier()
         t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            plan.apply_host_ptr(Bpin.data_ptr(), k, Cpin.data_ptr(), stream)
+        for i in range(n_e2e):
+            plan.apply_host_async(Bpin[i % 2], Cpin[i % 2], k, stream)
+        plan.host_sync()
         e2e_t = (time.perf_counter() - t0) / n_e2e
+        t0 = time.perf_counter()
+        for _ in range(5):
+            plan.apply_host_ptr(Bpin[0].data_ptr(), k, Cpin[0].data_ptr(), stream)
+        sync_t = (time.perf_counter() - t0) / 5
         if world > 1:
-            t = torch.tensor([e2e_t], device="cuda")
+            t = torch.tensor([e2e_t, sync_t], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_t = float(t.item())
+            e2e_t, sync_t = float(t[0].item()), float(t[1].item())
         line["e2e"] = {"value": round(tr.flops * world / e2e_t / 1e9, 3), "unit": "GFlop/s",
-                       "h2d_bytes_per_step": 8 * A.n_cols * k, "d2h_bytes_per_step": 8 * A.n_rows * k}
+                       "h2d_bytes_per_step": 8 * A.n_cols * k, "d2h_bytes_per_step": 8 * A.n_rows * k,
+                       "api": "spmv_apply_host_async, pipelined, host_sync at the end",
+                       "synchronous_call_gflops": round(tr.flops * world / sync_t / 1e9, 3)}
     if not args.no_forms and args.workload.startswith("poisson3d"):
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
+    if args.selector and k == 1:
+        line["selector"] = plan_selector(args, A, timer, stream, tr, spmv)
     if rank == 0 and not args.no_cpu:
         import oracle
         ts = time_oracle(lambda: oracle.spmv(A, Bh) if k == 1 else oracle.spmm(A, Bh), 3, budget_s=30.0)
@@ -453,6 +471,8 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
             t = med(lambda: batch.apply(stream))
             forms[f"batched_fixed_{spmv.POLICY_NAMES[pol]}"] = {"gflops": round(flops / t / 1e9, 1)}
         line["forms"] = forms
+    if args.selector:
+        line["selector"] = batch_selector(args, As, batch, timer, stream, flops, spmv)
     if rank == 0 and not args.no_cpu:
         import oracle
         sub = min(len(As), 64)
@@ -464,6 +484,59 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     for p in plans:
         p.close()
     return line
+
+
+def batch_selector(args, As, batch, timer, stream, flops, spmv):
+    """Cost model for batch members: trained on generated members, evaluated on
+    every n-th member against the exhaustive sweep of all row policies, then
+    used to pick every member's policy in the full batched launch."""
+    import tempfile
+    from paper_1101_0091_gb300 import selector as sel
+    t0 = time.time()
+    train = sel.build_dataset(sel.batch_training_matrices(args.selector_train), "batch", stream)
+    cm = sel.train_model(train, len(sel.BATCH_POLICIES))
+    ckpt = os.path.join(tempfile.gettempdir(), "spmv_batch_cost_model.bin")
+    cm.save(ckpt)
+    t_train = time.time() - t0
+    idx = list(range(0, len(As), args.selector_stride))
+    ev = sel.build_dataset([As[i] for i in idx], "batch", stream)
+    choice, _ = cm.select(ev.X)
+    names = [p[0] for p in sel.BATCH_POLICIES]
+    best_fixed = int(ev.times.sum(axis=0).argmin())
+    Xall = np.array([spmv.features(A, 4) for A in As])
+    ch_all, _ = cm.select(Xall)
+    batch.set_policies([sel.BATCH_POLICIES[c][1] for c in ch_all])
+    t_sel = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
+    batch.set_policies([sel.BATCH_POLICIES[sel.BATCH_DEFAULT][1]] * len(As))
+    t_def = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
+    return {"training_members": args.selector_train, "train_and_sweep_s": round(t_train, 1),
+            "evaluated_members": len(idx), "regret_learned": sel.regret(ev.times, choice),
+            "regret_default_" + names[sel.BATCH_DEFAULT]: sel.fixed_choice_regret(ev.times, sel.BATCH_DEFAULT),
+            "regret_best_fixed_" + names[best_fixed]: sel.fixed_choice_regret(ev.times, best_fixed),
+            "choices_all_members": {names[v]: int((ch_all == v).sum()) for v in range(len(names))},
+            "batch_gflops_learned_policies": round(flops / t_sel / 1e9, 1),
+            "batch_gflops_default_policy": round(flops / t_def / 1e9, 1)}
+
+
+def plan_selector(args, A, timer, stream, tr, spmv):
+    """Cost model for single products: trained on generated matrices, picks the
+    kernel for this workload; its time against the default kernel and the sweep."""
+    import torch
+    from paper_1101_0091_gb300 import selector as sel
+    t0 = time.time()
+    train = sel.build_dataset(sel.training_matrices(args.selector_train, seed=1000, scale=0.25), "plan", stream)
+    cm = sel.train_model(train, len(sel.PLAN_VARIANTS))
+    t_train = time.time() - t0
+    sweep = sel.sweep_plan(A, stream)
+    choice, _ = cm.select(spmv.features(A, 1))
+    c = int(choice[0])
+    names = [v[0] for v in sel.PLAN_VARIANTS]
+    return {"training_matrices": args.selector_train, "train_and_sweep_s": round(t_train, 1),
+            "chosen": names[c], "best_in_sweep": names[int(sweep.argmin())],
+            "gflops_chosen": round(tr.flops / sweep[c] / 1e9, 1),
+            "gflops_default_" + names[sel.PLAN_DEFAULT]: round(tr.flops / sweep[sel.PLAN_DEFAULT] / 1e9, 1),
+            "gflops_best": round(tr.flops / sweep.min() / 1e9, 1),
+            "regret": round(float(sweep[c] / sweep.min() - 1), 4)}
 
 
 def main():

@@ -139,6 +139,20 @@ spmv_status spmv_apply_split(spmv_handle h, double* B_dev, const double* B_halo_
 spmv_status spmv_apply_host(spmv_handle h, const double* B_host, int32_t k, double* C_host,
                             void* stream);
 
+/* Pipelined end-to-end products from PAGE-LOCKED host buffers.  Each call
+ * enqueues one step and returns: the copy of B_host (n_cols*k) into one of two
+ * plan-owned device buffer sets on an internal copy-in stream, the product on
+ * `stream` once that copy is in, and the copy of the result into C_host
+ * (n_rows*k, row-major, ldc = k) on an internal copy-out stream.  Steps
+ * alternate between the two buffer sets, so the copy-in of step i+1 and the
+ * copy-out of step i-1 run while step i multiplies (the paper's overlap of
+ * transfers and computation, Sec. 3.2, applied to the host link).  B_host and
+ * C_host must stay valid until spmv_host_sync returns. */
+spmv_status spmv_apply_host_async(spmv_handle h, const double* B_host, int32_t k, double* C_host, void* stream);
+
+/* Wait for every step enqueued by spmv_apply_host_async on this plan. */
+spmv_status spmv_host_sync(spmv_handle h);
+
 /* Switch the active variant (building its format on first use: the row
  * blocks of CRS_STAGED, or SELL-C-sigma with the given sigma). */
 spmv_status spmv_set_variant(spmv_handle h, int32_t variant, int32_t sell_sigma);

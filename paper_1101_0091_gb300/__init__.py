@@ -104,6 +104,13 @@ class Plan:
     def apply_host_ptr(self, B_ptr: int, k: int, C_ptr: int, stream=None) -> None:
         spmv_apply_host(self.handle, B_ptr, k, C_ptr, _stream_handle(stream))
 
+    def apply_host_async(self, B_pinned, C_pinned, k: int = 1, stream=None) -> None:
+        """Enqueue one pipelined end-to-end step (page-locked torch CPU tensors)."""
+        _b.spmv_apply_host_async(self.handle, B_pinned.data_ptr(), k, C_pinned.data_ptr(), _stream_handle(stream))
+
+    def host_sync(self) -> None:
+        _b.spmv_host_sync(self.handle)
+
     def set_variant(self, variant: int, sell_sigma: int = 1) -> None:
         spmv_set_variant(self.handle, variant, sell_sigma)
 

@@ -172,3 +172,15 @@ def spmv_get_tuning(h) -> spmv_tuning:
     t = spmv_tuning()
     _check(load().spmv_get_tuning(h, ctypes.byref(t)))
     return t
+
+
+_SIGS["spmv_apply_host_async"] = ([_vp, _vp, _i32, _vp, _vp], ctypes.c_int)
+_SIGS["spmv_host_sync"] = ([_vp], ctypes.c_int)
+
+
+def spmv_apply_host_async(h, B_host: int, k: int, C_host: int, stream: int = 0) -> None:
+    _check(load().spmv_apply_host_async(h, B_host, k, C_host, stream))
+
+
+def spmv_host_sync(h) -> None:
+    _check(load().spmv_host_sync(h))

@@ -108,7 +108,28 @@ struct spmv_plan {
   double* d_C = nullptr;
   int64_t scratch_k = 0;
   spmv_tuning tuning{};
+  // pipelined host steps: two device buffer sets, copy-in / copy-out streams
+  struct Pipe {
+    double* B[2] = {nullptr, nullptr};
+    double* C[2] = {nullptr, nullptr};
+    int64_t k = 0;
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t in_done[2] = {nullptr, nullptr}, kern_done[2] = {nullptr, nullptr}, out_done[2] = {nullptr, nullptr};
+    int64_t step = 0;
+  } pipe;
 };
+
+static void free_pipe(spmv_plan* p) {
+  auto& q = p->pipe;
+  for (int s = 0; s < 2; ++s) {
+    if (q.in_done[s]) cudaEventDestroy(q.in_done[s]);
+    if (q.kern_done[s]) cudaEventDestroy(q.kern_done[s]);
+    if (q.out_done[s]) cudaEventDestroy(q.out_done[s]);
+  }
+  if (q.in) cudaStreamDestroy(q.in);
+  if (q.out) cudaStreamDestroy(q.out);
+  q = spmv_plan::Pipe{};
+}
 
 static void apply_tuning(spmv_plan* p) {
   p->A.prefetch = p->tuning.prefetch_distance;
@@ -335,8 +356,75 @@ spmv_status spmv_destroy(spmv_handle h) {
   cudaDeviceSynchronize();
   if (h->ev_main) cudaEventDestroy(h->ev_main);
   if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+  free_pipe(h);
   h->arena.free_all();
   delete h;
+  return SPMV_OK;
+}
+
+spmv_status spmv_apply_host_async(spmv_handle h, const double* B_host, int32_t k, double* C_host, void* stream) {
+  if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
+  if (k < 1 || k > h->opt.max_k) return fail(SPMV_ERR_ARG, "k out of range 1..max_k");
+  if ((!B_host && h->host.n_cols > 0) || (!C_host && h->host.n_rows > 0)) return fail(SPMV_ERR_ARG, "NULL buffer");
+  DeviceGuard g(h->device);
+  auto& q = h->pipe;
+  if (q.k < k) {  // (re)allocate both buffer sets for this k
+    if (q.in) {
+      SPMV_CUDA(cudaStreamSynchronize(q.in));
+      SPMV_CUDA(cudaStreamSynchronize(q.out));
+    }
+    for (int s = 0; s < 2; ++s) {
+      if (q.B[s]) h->arena.release(q.B[s]);
+      if (q.C[s]) h->arena.release(q.C[s]);
+      q.B[s] = q.C[s] = nullptr;
+    }
+    q.k = 0;
+    for (int s = 0; s < 2; ++s) {
+      void *b, *c;
+      SPMV_CUDA(h->arena.alloc(&b, sizeof(double) * (size_t)(h->host.n_cols * k)));
+      q.B[s] = (double*)b;
+      SPMV_CUDA(h->arena.alloc(&c, sizeof(double) * (size_t)(h->host.n_rows * k)));
+      q.C[s] = (double*)c;
+    }
+    q.k = k;
+  }
+  if (!q.in) {
+    SPMV_CUDA(cudaStreamCreateWithFlags(&q.in, cudaStreamNonBlocking));
+    SPMV_CUDA(cudaStreamCreateWithFlags(&q.out, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.in_done[s], cudaEventDisableTiming));
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.kern_done[s], cudaEventDisableTiming));
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.out_done[s], cudaEventDisableTiming));
+    }
+  }
+  const int s = (int)(q.step & 1);
+  cudaStream_t cs = (cudaStream_t)stream;
+  // copy in once the product two steps back has finished reading this buffer set
+  SPMV_CUDA(cudaStreamWaitEvent(q.in, q.kern_done[s], 0));
+  SPMV_CUDA(cudaMemcpyAsync(q.B[s], B_host, sizeof(double) * (size_t)(h->host.n_cols * k), cudaMemcpyHostToDevice,
+                            q.in));
+  SPMV_CUDA(cudaEventRecord(q.in_done[s], q.in));
+  // multiply once the operand is in and the result two steps back has been copied out
+  SPMV_CUDA(cudaStreamWaitEvent(cs, q.in_done[s], 0));
+  SPMV_CUDA(cudaStreamWaitEvent(cs, q.out_done[s], 0));
+  spmv_status st = spmv_apply_block(h, q.B[s], k, k, q.C[s], k, stream);
+  if (st != SPMV_OK) return st;
+  SPMV_CUDA(cudaEventRecord(q.kern_done[s], cs));
+  SPMV_CUDA(cudaStreamWaitEvent(q.out, q.kern_done[s], 0));
+  SPMV_CUDA(cudaMemcpyAsync(C_host, q.C[s], sizeof(double) * (size_t)(h->host.n_rows * k), cudaMemcpyDeviceToHost,
+                            q.out));
+  SPMV_CUDA(cudaEventRecord(q.out_done[s], q.out));
+  q.step += 1;
+  return SPMV_OK;
+}
+
+spmv_status spmv_host_sync(spmv_handle h) {
+  if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
+  DeviceGuard g(h->device);
+  if (h->pipe.in) {
+    SPMV_CUDA(cudaStreamSynchronize(h->pipe.in));
+    SPMV_CUDA(cudaStreamSynchronize(h->pipe.out));
+  }
   return SPMV_OK;
 }
 

@@ -226,3 +226,29 @@ def test_prefetch_tuning_keeps_results(lib, variant):
             assert np.array_equal(run(p, B), base)
         with pytest.raises(lib.SpmvError):
             p.set_tuning(prefetch_distance=-1)
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_pipelined_host_steps(lib, k):
+    """Pipelined end-to-end steps (two device buffer sets, copy-in/out streams)
+    give every step's own product, also when the buffers are reused."""
+    import torch
+    A = case("poisson40")
+    steps = 5
+    Bs = [gen.uniform(A.n_cols * k, seed=50 + i).reshape(A.n_cols, k) if k > 1 else gen.uniform(A.n_cols, seed=50 + i)
+          for i in range(steps)]
+    Bp = [torch.from_numpy(B.copy()).pin_memory() for B in Bs]
+    Cp = [torch.full(B.shape[:1] if k == 1 else (A.n_rows, k), float("nan"), dtype=torch.float64).pin_memory()
+          for B in Bs]
+    with lib.Plan.from_csr(A) as p:
+        for i in range(steps):
+            p.apply_host_async(Bp[i], Cp[i], k)
+        p.host_sync()
+        for i in range(steps):
+            assert_close(Cp[i].numpy(), A, Bs[i])
+        # same host buffers again: results are overwritten in step order
+        for i in range(steps):
+            p.apply_host_async(Bp[steps - 1 - i], Cp[i], k)
+        p.host_sync()
+        for i in range(steps):
+            assert_close(Cp[i].numpy(), A, Bs[steps - 1 - i])
