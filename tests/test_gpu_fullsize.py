@@ -97,3 +97,58 @@ def test_eigen_full_staged_and_sell(lib):
             p.apply(Bd, C)
             p.check()
             check_sampled(host(C), A, B, rows)
+
+
+def test_batch512_full_size_sampled(lib):
+    """The 512-member uneven batch, k = 4, in the configuration the benchmark
+    times (sorted policy, autotuned, graph replay), on 40 sampled rows per
+    member plus every row of the members' longest rows."""
+    import torch
+    As = [gen.powerlaw_batch_member(m) for m in range(512)]
+    Bs = [gen.rhs_block(A.n_cols, 4, seed=0, stream=2 * m + 1) for m, A in enumerate(As)]
+    plans = [lib.Plan.from_csr(A) for A in As]
+    Bd = [dev(B) for B in Bs]
+    Cd = [torch.full((A.n_rows, 4), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+    with lib.Batch(plans, 4, [lib.SPMV_BATCH_SORTED] * len(As)) as b:
+        b.set_io(Bd, Cd)
+        b.autotune(reps=1)
+        for _ in range(2):
+            b.apply()
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    for m, (A, B, C) in enumerate(zip(As, Bs, Cd)):
+        y = host(C)
+        assert not np.isnan(y).any(), m
+        L = A.row_lengths()
+        rows = np.unique(np.concatenate([rng.integers(0, A.n_rows, 40), np.argsort(L)[-3:]]))
+        S = sub_csr(A, rows)
+        ref = oracle.spmm(S, B)
+        assert oracle.max_err_ratio(y[rows], ref, oracle.abs_scale(S, B), TOL_FP64) <= 1.0, m
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("k", [1, 4, 8, 16])
+def test_laplace256_block_precision(lib, k, fp32):
+    """The 2D Laplacian workload with k right-hand sides, FP64 vs FP32 values:
+    its values (4, -1) are exact in FP32, so both forms meet the FP64 bound."""
+    A = gen.laplace2d(256)
+    B = gen.rhs_block(A.n_cols, k, seed=k) if k > 1 else gen.uniform(A.n_cols, seed=1)
+    with lib.Plan.from_csr(A, val_fp32=fp32) as p:
+        y = run_block(p, B)
+    ref = oracle.spmm(A, B.reshape(A.n_cols, -1))
+    S = oracle.abs_scale(A, B.reshape(A.n_cols, -1))
+    assert oracle.max_err_ratio(y.reshape(A.n_rows, -1), ref, S, TOL_FP64) <= 1.0
+
+
+def run_block(p, B):
+    import torch
+    Bd = dev(B)
+    C = torch.full(B.shape if B.ndim == 2 else (p.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+    if B.ndim == 1:
+        p.apply(Bd, C)
+    else:
+        p.apply_block(Bd, C)
+    p.check()
+    return host(C)
