@@ -350,6 +350,8 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
                        "synchronous_call_gflops": round(tr.flops * world / sync_t / 1e9, 3)}
     if not args.no_forms and args.workload.startswith("poisson3d"):
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
+    if not args.no_forms and args.workload == "laplace2d_256":
+        line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
     if args.selector and k == 1:
         line["selector"] = plan_selector(args, A, timer, stream, tr, spmv)
     if rank == 0 and not args.no_cpu:
@@ -393,6 +395,41 @@ def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
         forms["split_serial_copy"] = {"gflops": round(tr.flops / t_ser / 1e9, 1), "ms": round(t_ser * 1e3, 4)}
         forms["split_penalty_eq2_model"] = round(pm.split_penalty(A.nnz / A.n_rows), 4)
     return forms
+
+
+def block_precision_forms(A, torch, spmv, pm, stream):
+    """k right-hand sides x value storage on the L2-resident 2D Laplacian: warm
+    (back to back) and cold (L2 flushed by a 256 MB write before each launch)
+    median CUDA-event times of the plan's default kernel."""
+    import gen
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for f32 in (False, True):
+        with spmv.Plan.from_csr(A, val_fp32=f32) as p:
+            for k in (1, 4, 8, 16):
+                Bh = gen.uniform(A.n_cols, seed=0) if k == 1 else gen.rhs_block(A.n_cols, k, seed=0)
+                B = torch.from_numpy(Bh).cuda()
+                C = torch.empty((A.n_rows,) if k == 1 else (A.n_rows, k), dtype=torch.float64, device="cuda")
+                stream.wait_stream(torch.cuda.current_stream())
+                fn = (lambda: p.apply(B, C, stream)) if k == 1 else (lambda: p.apply_block(B, C, k, stream))
+                warm, cold = [], []
+                for i in range(60):
+                    if i % 2:
+                        with torch.cuda.stream(stream):
+                            flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    stream.synchronize()
+                    (cold if i % 2 else warm).append(e0.elapsed_time(e1) / 1e3)
+                tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k, val_bytes=4 if f32 else 8)
+                tw, tc = statistics.median(warm[5:]), statistics.median(cold[5:])
+                out[f"k{k}_{'f32' if f32 else 'f64'}val"] = {
+                    "warm_gflops": round(tr.flops / tw / 1e9, 1), "warm_us": round(tw * 1e6, 2),
+                    "cold_gflops": round(tr.flops / tc / 1e9, 1), "cold_us": round(tc * 1e6, 2),
+                    "cold_hbm_gbs": round(tr.bytes_min / tc / 1e9, 1)}
+    return out
 
 
 def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):

@@ -176,6 +176,20 @@ spmv_status spmv_get_tuning(spmv_handle h, spmv_tuning* t);
  * reported a failed bounded wait, else SPMV_OK. */
 spmv_status spmv_check(spmv_handle h, void* stream);
 
+/* Host-side bounded wait: poll until the work on `stream` is done, giving up
+ * after timeout_ms with SPMV_ERR_TIMEOUT (the work keeps running; call again).
+ * The paper's codes wait on MPI requests; this is the host's deadline. */
+spmv_status spmv_wait(void* stream, int32_t timeout_ms);
+
+/* Self-test of the failure path of the bounded device wait (no fault, no
+ * hang): one CTA waits on an mbarrier phase that nothing completes, with the
+ * same bounded wait as CRS_STAGED's bulk copies but a limit of limit_us
+ * microseconds (1 .. 1,000,000); it gives up, records the timeout in a status
+ * word and exits.  Returns SPMV_ERR_TIMEOUT when the kernel reported the
+ * timeout (the expected outcome), SPMV_OK if the wait completed.  Synchronous
+ * on the current device. */
+spmv_status spmv_selftest_wait_timeout(int32_t limit_us);
+
 /* Copy the built SELL-C-sigma arrays to host arrays sized from spmv_info:
  * perm[n_rows], chunk_ptr[sell_chunks+1], chunk_len[sell_chunks],
  * sell_col[sell_slots], sell_val[sell_slots] (any may be NULL to skip).

@@ -14,6 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import _binding as _b
+from ._binding import spmv_apply_host_async, spmv_host_sync, spmv_selftest_wait_timeout, spmv_wait  # noqa: F401
 from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_block, spmv_apply_host,  # noqa: F401
                        spmv_apply_split, spmv_check, spmv_create, spmv_default_options, spmv_destroy,
                        spmv_get_info, spmv_last_error, spmv_options, spmv_sell_export, spmv_set_variant,

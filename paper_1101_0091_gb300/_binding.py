@@ -184,3 +184,15 @@ def spmv_apply_host_async(h, B_host: int, k: int, C_host: int, stream: int = 0) 
 
 def spmv_host_sync(h) -> None:
     _check(load().spmv_host_sync(h))
+
+
+_SIGS["spmv_wait"] = ([_vp, _i32], ctypes.c_int)
+_SIGS["spmv_selftest_wait_timeout"] = ([_i32], ctypes.c_int)
+
+
+def spmv_wait(stream: int, timeout_ms: int) -> None:
+    _check(load().spmv_wait(stream, timeout_ms))
+
+
+def spmv_selftest_wait_timeout(limit_us: int) -> None:
+    _check(load().spmv_selftest_wait_timeout(limit_us))

@@ -77,8 +77,10 @@ def test_poisson280_fp32_values(lib, poisson280):
         p.apply(dev(B), C)
         p.check()
         y = host(C)
-    check_sampled(y, A, B, rows, f32val=True)
-    check_sampled(y, A, B, rows, tol=TOL_FP32VAL)
+    r32 = check_sampled(y, A, B, rows, f32val=True)
+    r64 = check_sampled(y, A, B, rows, tol=TOL_FP32VAL)
+    print(f"poisson280 FP32 values: max |err| / (2e-7 sum|ab|) vs the FP64 oracle = {r64:.4f}; "
+          f"vs the oracle's FP32-value loop / (1e-13 sum|ab|) = {r32:.4f}")
 
 
 def test_eigen_full_staged_and_sell(lib):
@@ -139,7 +141,12 @@ def test_laplace256_block_precision(lib, k, fp32):
         y = run_block(p, B)
     ref = oracle.spmm(A, B.reshape(A.n_cols, -1))
     S = oracle.abs_scale(A, B.reshape(A.n_cols, -1))
-    assert oracle.max_err_ratio(y.reshape(A.n_rows, -1), ref, S, TOL_FP64) <= 1.0
+    Y = y.reshape(A.n_rows, -1)
+    per_col = [oracle.max_err_ratio(Y[:, c], ref[:, c], S[:, c], TOL_FP64) for c in range(ref.shape[1])]
+    abs_err = np.abs(Y - ref).max(axis=0)
+    print(f"laplace256 k={k} {'f32' if fp32 else 'f64'} values: per-column max |err|/(1e-13*sum|ab|) "
+          f"{np.round(per_col, 4).tolist()}, max |err| {abs_err.tolist()}")
+    assert max(per_col) <= 1.0
 
 
 def run_block(p, B):
