@@ -235,6 +235,25 @@ def reference_arm(args):
     return 0
 
 
+def all_max(values, world: int):
+    """Element-wise maximum over ranks (replicas: the slowest rank sets the
+    time).  CUDA tensors under NCCL, CPU tensors under gloo."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def replica_value(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 class Timer:
     """CUDA-event timing of `steps` calls on one stream, with a barrier and a
     synchronize on both sides and nvidia-smi clock samples inside the region."""
@@ -273,11 +292,7 @@ class Timer:
         if clk:
             clk.__exit__(None, None, None)
         per = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
-        total_ms = ev[0].elapsed_time(ev[-1])
-        if self.world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = all_max([ev[0].elapsed_time(ev[-1])], self.world)[0]
         return {"total_ms": total_ms, "per_ms": per, "wall_s": t1 - t0,
                 "clocks": clk.summary(t0, t1) if clk else None}
 
@@ -302,7 +317,8 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     achieved = tr.bytes_min / kern_s / 1e9
     kname = "sell" if args.variant.startswith("sell") else args.variant
     line = {
-        "metric": METRIC, "value": round(tr.flops * world / t_step / 1e9, 3), "unit": "GFlop/s", "n_gpus": world,
+        "metric": METRIC, "value": round(replica_value(tr.flops, t_step, world) / 1e9, 3), "unit": "GFlop/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": args.variant,
@@ -340,10 +356,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         for _ in range(5):
             plan.apply_host_ptr(Bpin[0].data_ptr(), k, Cpin[0].data_ptr(), stream)
         sync_t = (time.perf_counter() - t0) / 5
-        if world > 1:
-            t = torch.tensor([e2e_t, sync_t], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_t, sync_t = float(t[0].item()), float(t[1].item())
+        e2e_t, sync_t = all_max([e2e_t, sync_t], world)
         line["e2e"] = {"value": round(tr.flops * world / e2e_t / 1e9, 3), "unit": "GFlop/s",
                        "h2d_bytes_per_step": 8 * A.n_cols * k, "d2h_bytes_per_step": 8 * A.n_rows * k,
                        "api": "spmv_apply_host_async, pipelined, host_sync at the end",
@@ -455,7 +468,8 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     hbm, hbm_kind = measured_hbm()
     achieved_gf = flops / kern_s / 1e9
     line = {
-        "metric": METRIC, "value": round(flops * world / t_step / 1e9, 3), "unit": "GFlop/s", "n_gpus": world,
+        "metric": METRIC, "value": round(replica_value(flops, t_step, world) / 1e9, 3), "unit": "GFlop/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "members": len(As),
