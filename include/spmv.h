@@ -301,7 +301,7 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b);
  *
  * Scratch: one static 8 MiB device array per device that loads the library,
  * held until the process exits, holding the work counter, the member table and
- * the work list.  Limits: count <= 8192 members and at most 327,669 work
+ * the work list.  Limits: count <= 8192 members and at most 245,752 work
  * items (one item per 32 warp passes: 1024 rows at 1 lane per row), beyond
  * which the call returns SPMV_ERR_ARG without touching the device.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress);

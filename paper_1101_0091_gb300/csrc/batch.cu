@@ -49,13 +49,13 @@ static void cut_items(const int32_t* rp, int64_t p0, int64_t p1, int mat, int L,
   int64_t s = p0, work = 0;
   for (int64_t p = p0; p < p1; ++p) {
     if (p > s && (work >= item_nnz || p - s >= rows_cap)) {
-      out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p, (int32_t)len, (int16_t)L, (int16_t)mode, 0});
+      out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p, (int32_t)len, (int16_t)L, (int16_t)mode, 0, 0});
       s = p;
       work = 0;
     }
     work += mode == 1 ? std::max<int64_t>(len, 1) : (mode == 2 ? len : std::max<int64_t>(rp[p + 1] - rp[p], 1));
   }
-  if (p1 > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p1, (int32_t)len, (int16_t)L, (int16_t)mode, 0});
+  if (p1 > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p1, (int32_t)len, (int16_t)L, (int16_t)mode, 0, 0});
 }
 
 // Length-sorted SELL-32 copy of the rows with at most 32 entries (sorted
@@ -111,18 +111,24 @@ static void append_sorted_sell(const int32_t* rp, const int32_t* col, const doub
 }
 
 // Items over chunks [c0, c0 + nc) of the sorted copy, about item_nnz slots each.
+// (An item never mixes chunk lengths, so it carries the length and the first
+// slot and the kernel needs no per-chunk metadata.)
 static void cut_chunk_items(const SortedSell& S, int64_t c0, int64_t nc, int mat, int item_nnz,
                             std::vector<BatchItem>& out) {
   int64_t s = c0, work = 0;
+  auto emit = [&](int64_t e) {
+    out.push_back(BatchItem{mat, (int32_t)s, (int32_t)e, S.chunk_len[(size_t)s], (int16_t)1, (int16_t)3, 0,
+                            S.chunk_ptr[(size_t)s]});
+  };
   for (int64_t c = c0; c < c0 + nc; ++c) {
-    if (c > s && work >= item_nnz) {
-      out.push_back(BatchItem{mat, (int32_t)s, (int32_t)c, 0, (int16_t)1, (int16_t)3, 0});
+    if (c > s && (work >= item_nnz || S.chunk_len[(size_t)c] != S.chunk_len[(size_t)s])) {
+      emit(c);
       s = c;
       work = 0;
     }
     work += std::max<int64_t>(32 * (int64_t)S.chunk_len[(size_t)c], 32);
   }
-  if (c0 + nc > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)(c0 + nc), 0, (int16_t)1, (int16_t)3, 0});
+  if (c0 + nc > s) emit(c0 + nc);
 }
 
 void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, int item_nnz,

@@ -20,13 +20,15 @@ struct BatchMat {
 // mode 1: the rows listed at positions [p0, p1) of the (row, first entry)
 // list, all of length `len` (the length-binned rows of the adaptive policy).
 // mode 2: listed rows of unequal lengths (ends from row_ptr).
-// mode 3: chunks [p0, p1) of the length-sorted SELL-32 copy (sorted policy):
-// one lane per row, slots column-major inside a chunk.
+// mode 3: chunks [p0, p1) of the length-sorted SELL-32 copy (sorted policy),
+// all of length `len`, stored back to back from slot `base`: one lane per row,
+// slots column-major inside a chunk.
 // L lanes share one row; 32/L rows per warp pass.
 struct BatchItem {
   int32_t mat, p0, p1, len;
   int16_t lanes, mode;
   int32_t pad;
+  int64_t base;
 };
 
 // Length-sorted SELL-32 copy of the short rows of the members with the sorted
@@ -132,6 +134,59 @@ __device__ __forceinline__ void batch_rows(const BatchMat* __restrict__ Mp, cons
   }
 }
 
+// Chunks whose rows all have exactly LEN entries, CH chunks per step; returns
+// the first chunk left for the generic loop.  Same FMA order per row as the
+// generic loop.
+template <int LEN, int CH, int K, bool VEC>
+__device__ __forceinline__ int chunks_fixed(const BatchMat* __restrict__ Mp, const double* __restrict__ B,
+                                            int64_t ldb, const BatchSell& S, const BatchItem& item, int k,
+                                            int lane) {
+  int c = item.p0;
+  for (; c + CH - 1 < item.p1; c += CH) {
+    const int64_t s0 = item.base + (int64_t)(c - item.p0) * 32 * LEN + lane;
+    int r[CH];
+    double v[CH][LEN];
+    const double* b[CH][LEN];
+#pragma unroll
+    for (int h = 0; h < CH; ++h) {
+      r[h] = __ldg(S.perm + (int64_t)(c + h) * 32 + lane);
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) {
+        const int64_t slot = s0 + (int64_t)(h * LEN + j) * 32;
+        v[h][j] = ldcs(S.val + slot);
+        b[h][j] = B + (int64_t)ldcs(S.col + slot) * ldb;
+      }
+    }
+    double g[CH][LEN][K];
+#pragma unroll
+    for (int h = 0; h < CH; ++h)
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) gather_row<K, VEC>(b[h][j], k, g[h][j]);
+#pragma unroll
+    for (int h = 0; h < CH; ++h) {
+      double acc[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc[q] = 0.0;
+#pragma unroll
+      for (int j = 0; j < LEN; ++j)
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[q] = fma(v[h][j], g[h][j][q], acc[q]);
+      if (r[h] < 0) continue;
+      double* out = Mp->C + (int64_t)r[h] * Mp->ldc;
+      if (VEC && K >= 2) {
+#pragma unroll
+        for (int q = 0; q + 1 < K; q += 2)
+          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          if (q < k) out[q] = acc[q];
+      }
+    }
+  }
+  return c;
+}
+
 template <int K, bool VEC>
 __device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, const BatchSell& S,
                                              const BatchItem& item, int k, int lane) {
@@ -139,9 +194,16 @@ __device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, co
     const double* B;
     int64_t ldb;
   } M = {Mp->B, Mp->ldb};  // only what the inner loop needs stays in registers
-  for (int c = item.p0; c < item.p1; ++c) {
-    const int len = __ldg(S.chunk_len + c);
-    const int64_t base = __ldg(S.chunk_ptr + c) + lane;
+  const int len = item.len;  // every chunk of the item has this length: no per-chunk metadata loads
+  int c = item.p0;
+  // short rows (most rows of a power-law matrix): a fixed length, several
+  // chunks per step, every load and gather of a step in flight together
+  if (len == 1) c = chunks_fixed<1, K <= 4 ? 4 : 2, K, VEC>(Mp, M.B, M.ldb, S, item, k, lane);
+  else if (len == 2) c = chunks_fixed<2, K <= 4 ? 2 : 1, K, VEC>(Mp, M.B, M.ldb, S, item, k, lane);
+  else if (len == 3 && K <= 4) c = chunks_fixed<3, 1, K, VEC>(Mp, M.B, M.ldb, S, item, k, lane);
+  else if (len == 4 && K <= 4) c = chunks_fixed<4, 1, K, VEC>(Mp, M.B, M.ldb, S, item, k, lane);
+  for (; c < item.p1; ++c) {
+    const int64_t base = item.base + (int64_t)(c - item.p0) * 32 * len + lane;
     const int r = __ldg(S.perm + (int64_t)c * 32 + lane);
     double acc[K];
 #pragma unroll
