@@ -198,3 +198,27 @@ def csr_from_lengths(lengths, n_cols: int, seed: int, integer: bool = False) -> 
     va = (rng.integers(-1024, 1025, size=nnz).astype(np.float64) if integer
           else rng.uniform(-1.0, 1.0, size=nnz))
     return CSR(len(lengths), n_cols, rp, ci, va)
+
+
+def symmetric_from(A: CSR, seed: int = 0, shuffle: bool = False) -> CSR:
+    """Symmetric square matrix (n = A.n_rows) from A's entries with
+    row <= col < n: each such entry (i, j, v) is kept and, off the diagonal,
+    mirrored as (j, i, v), so duplicates mirror one to one.  Entries of a row
+    are in ascending column order (stable), or in a seeded random order."""
+    n = A.n_rows
+    r = np.repeat(np.arange(n, dtype=np.int64), np.diff(A.row_ptr).astype(np.int64))
+    c = A.col_idx.astype(np.int64)
+    v = A.val.astype(np.float64)
+    keep = (c >= r) & (c < n)
+    r, c, v = r[keep], c[keep], v[keep]
+    off = r != c
+    R = np.concatenate([r, c[off]])
+    Cc = np.concatenate([c, r[off]])
+    V = np.concatenate([v, v[off]])
+    if shuffle:
+        order = np.lexsort((np.random.default_rng(seed).random(len(R)), R))
+    else:
+        order = np.lexsort((Cc, R))
+    rp = np.zeros(n + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(np.bincount(R, minlength=n))
+    return CSR(n, n, rp, Cc[order].astype(np.int32), V[order])

@@ -7,8 +7,9 @@ does, and it shares no code with that library.
 
 * ``oracle.c`` (FP64, single thread, -ffp-contract=off): the CRS loop of
   Sec. 1.2, its k-RHS and FP32-value forms, the tolerance scale sum |a*b|, the
-  SELL-C-sigma builder and product, and the local/halo split builder and
-  product of Sec. 3.1.
+  SELL-C-sigma builder and product, the local/halo split builder and
+  product of Sec. 3.1, and the symmetric-CRS test, upper-triangle builder and
+  product of Sec. 1.3.1.
 * ``features.py`` (numpy): matrix features that feed the cost model.
 * ``mlp.py`` (numpy FP64): the cost model's forward, backward and Adam step.
 
@@ -60,6 +61,12 @@ def _load():
             lib.oracle_split_count.restype = i64
             lib.oracle_split_fill.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
             lib.oracle_split_spmv.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
+            lib.oracle_is_symmetric.argtypes = [i64, i64, vp, vp, vp]
+            lib.oracle_is_symmetric.restype = ctypes.c_int
+            lib.oracle_sym_count.argtypes = [i64, vp, vp]
+            lib.oracle_sym_count.restype = i64
+            lib.oracle_sym_fill.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+            lib.oracle_sym_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -192,6 +199,49 @@ def split_spmv(A_rows: int, S: Split, B) -> np.ndarray:
                               S.loc_val.ctypes.data, len(S.halo_rows), S.halo_rows.ctypes.data,
                               S.halo_row_ptr.ctypes.data, S.halo_col.ctypes.data,
                               S.halo_val.ctypes.data, pB, C.ctypes.data)
+    return C
+
+
+class Sym:
+    """Symmetric CRS: the entries on and above the diagonal of each row, in
+    their order in the row (row_ptr[n_rows+1], col[nnz_u], val[nnz_u])."""
+
+    def __init__(self, n_rows, row_ptr, col, val):
+        self.n_rows, self.row_ptr, self.col, self.val = n_rows, row_ptr, col, val
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+
+def is_symmetric(A) -> bool:
+    """Square, and every strictly-upper entry (i, j, v) mirrored one to one by a
+    strictly-lower entry (j, i, v) (values compared with -0.0 == +0.0)."""
+    keep, (rp, ci, va) = _csr(A)
+    r = _load().oracle_is_symmetric(A.n_rows, A.n_cols, rp, ci, va)
+    if r < 0:
+        raise MemoryError("oracle_is_symmetric: scratch allocation failed")
+    return bool(r)
+
+
+def sym_build(A) -> Sym:
+    """Upper triangle (diagonal included) of a symmetric CRS matrix (Sec. 1.3.1)."""
+    lib = _load()
+    keep, (rp, ci, va) = _csr(A)
+    n = lib.oracle_sym_count(A.n_rows, rp, ci)
+    S = Sym(A.n_rows, np.empty(A.n_rows + 1, np.int32), np.empty(n, np.int32), np.empty(n, np.float64))
+    lib.oracle_sym_fill(A.n_rows, rp, ci, va, S.row_ptr.ctypes.data, S.col.ctypes.data, S.val.ctypes.data)
+    return S
+
+
+def sym_spmv(S: Sym, B) -> np.ndarray:
+    """C = A*B from the stored triangle: each stored u_ij adds u_ij*B_j to C_i
+    and, off the diagonal, u_ij*B_i to C_j; rows in order."""
+    Bc, pB = _c(B, np.float64)
+    assert Bc.shape[0] >= S.n_rows
+    C = np.empty(S.n_rows, dtype=np.float64)
+    _load().oracle_sym_spmv(S.n_rows, S.row_ptr.ctypes.data, S.col.ctypes.data, S.val.ctypes.data, pB,
+                            C.ctypes.data)
     return C
 
 

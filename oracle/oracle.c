@@ -252,3 +252,123 @@ void oracle_split_spmv(int64_t n_rows, const int32_t* loc_row_ptr, const int32_t
     C[halo_rows[t]] = C[halo_rows[t]] + s;
   }
 }
+
+/* ---------------------------------------------------------------------------
+ * Symmetric CRS (Sec. 1.3.1): a real symmetric matrix is fully described by
+ * the entries on and above the diagonal, which roughly halves the stored
+ * val/col_idx volume.  The paper gives no code for it; the definitions below
+ * are the plain ones.
+ * --------------------------------------------------------------------------- */
+
+/* One off-diagonal entry as (r, c, key); the key is the value's bit pattern
+ * with -0.0 mapped to +0.0, so that equal values compare equal. */
+typedef struct {
+  int64_t r, c;
+  uint64_t key;
+} sym_triple;
+
+static uint64_t value_key(double v) {
+  uint64_t b;
+  if (v == 0.0) v = 0.0;  /* -0.0 -> +0.0 */
+  memcpy(&b, &v, sizeof(b));
+  return b;
+}
+
+static int triple_cmp(const void* a, const void* b) {
+  const sym_triple* x = (const sym_triple*)a;
+  const sym_triple* y = (const sym_triple*)b;
+  if (x->r != y->r) return x->r < y->r ? -1 : 1;
+  if (x->c != y->c) return x->c < y->c ? -1 : 1;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return 0;
+}
+
+/* 1 if the matrix is square and every entry strictly above the diagonal,
+ * (i, j, v), is matched one to one by an entry (j, i, v) strictly below it
+ * (as multisets, so duplicates must mirror one to one); else 0.  -1 if the
+ * scratch allocation fails.  Entries strictly below the diagonal are listed
+ * transposed, both lists are sorted and compared. */
+int oracle_is_symmetric(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
+                        const double* val) {
+  if (n_rows != n_cols) return 0;
+  int64_t nu = 0, nl = 0;
+  for (int64_t i = 0; i < n_rows; ++i)
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+      if (col_idx[j] > i) ++nu;
+      if (col_idx[j] < i) ++nl;
+    }
+  if (nu != nl) return 0;
+  sym_triple* U = (sym_triple*)malloc(sizeof(sym_triple) * (size_t)(nu > 0 ? nu : 1));
+  sym_triple* L = (sym_triple*)malloc(sizeof(sym_triple) * (size_t)(nl > 0 ? nl : 1));
+  if (!U || !L) {
+    free(U);
+    free(L);
+    return -1;
+  }
+  int64_t pu = 0, pl = 0;
+  for (int64_t i = 0; i < n_rows; ++i)
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+      int64_t c = col_idx[j];
+      if (c > i) {
+        U[pu].r = i;
+        U[pu].c = c;
+        U[pu++].key = value_key(val[j]);
+      } else if (c < i) {
+        L[pl].r = c; /* transposed */
+        L[pl].c = i;
+        L[pl++].key = value_key(val[j]);
+      }
+    }
+  qsort(U, (size_t)nu, sizeof(sym_triple), triple_cmp);
+  qsort(L, (size_t)nl, sizeof(sym_triple), triple_cmp);
+  int same = 1;
+  for (int64_t t = 0; t < nu && same; ++t)
+    if (triple_cmp(U + t, L + t) != 0) same = 0;
+  free(U);
+  free(L);
+  return same;
+}
+
+/* Number of entries on or above the diagonal (col_idx >= row). */
+int64_t oracle_sym_count(int64_t n_rows, const int32_t* row_ptr, const int32_t* col_idx) {
+  int64_t n = 0;
+  for (int64_t i = 0; i < n_rows; ++i)
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+      if (col_idx[j] >= i) ++n;
+  return n;
+}
+
+/* The stored triangle: for every row, its entries with col_idx >= row, in
+ * the order they have in the row. */
+void oracle_sym_fill(int64_t n_rows, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                     int32_t* u_row_ptr, int32_t* u_col, double* u_val) {
+  int64_t p = 0;
+  u_row_ptr[0] = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+      if (col_idx[j] >= i) {
+        u_col[p] = col_idx[j];
+        u_val[p++] = val[j];
+      }
+    u_row_ptr[i + 1] = (int32_t)p;
+  }
+}
+
+/* Product from the stored triangle, rows in order: a stored entry u(i,j)
+ * adds u(i,j)*B(j) to C(i) and, when j != i, its mirror u(i,j)*B(i) to C(j).
+ * C starts at +0.0. */
+void oracle_sym_spmv(int64_t n_rows, const int32_t* u_row_ptr, const int32_t* u_col, const double* u_val,
+                     const double* B, double* C) {
+  for (int64_t i = 0; i < n_rows; ++i) C[i] = 0.0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    for (int64_t j = u_row_ptr[i]; j < u_row_ptr[i + 1]; ++j) {
+      int64_t c = u_col[j];
+      double prod = u_val[j] * B[c];
+      C[i] = C[i] + prod;
+      if (c != i) {
+        double mirror = u_val[j] * B[i];
+        C[c] = C[c] + mirror;
+      }
+    }
+  }
+}
