@@ -45,7 +45,8 @@ WORKLOADS = {
                          "uniform columns, k=4 RHS each, one persistent graph-captured launch",
 }
 VARIANTS = {"crs_staged": (1, 1), "crs_l1": (2, 1), "crs_l2": (3, 1), "crs_l4": (4, 1), "crs_l8": (5, 1),
-            "crs_l16": (6, 1), "crs_l32": (7, 1), "sell_s1": (8, 1), "sell_s256": (8, 256), "sell_s4096": (8, 4096)}
+            "crs_l16": (6, 1), "crs_l32": (7, 1), "sell_s1": (8, 1), "sell_s256": (8, 256), "sell_s4096": (8, 4096),
+            "sym": (9, 1)}
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
@@ -111,6 +112,7 @@ def kernel_fingerprint(files) -> str:
 KERNEL_SOURCES = {"crs_l1": ["k_lanes.cu", "device.cuh", "internal.h"],
                   "crs_staged": ["k_staged.cu", "device.cuh", "internal.h"],
                   "sell": ["k_sell.cu", "device.cuh", "internal.h"],
+                  "sym": ["k_sym.cu", "device.cuh", "internal.h"],
                   "batch": ["batch_kernel.cuh", "batch.cu", "device.cuh", "internal.h"]}
 
 
@@ -309,6 +311,8 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     stream.wait_stream(torch.cuda.current_stream())
     fn = (lambda: plan.apply(B, C, stream)) if k == 1 else (lambda: plan.apply_block(B, C, k, stream))
     tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k, val_bytes=4 if args.fp32_val else 8)
+    if vid == spmv.SPMV_SYM:
+        tr = pm.gpu_sym_min_traffic(A.n_rows, A.nnz, plan.info().sym_nnz, k=k, val_bytes=4 if args.fp32_val else 8)
     r = timer.run(fn, args.steps, args.warmup, sample_clocks=True)
     plan.check(stream)
     t_step = r["total_ms"] / 1e3 / args.steps
@@ -363,6 +367,8 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
                        "synchronous_call_gflops": round(tr.flops * world / sync_t / 1e9, 3)}
     if not args.no_forms and args.workload.startswith("poisson3d"):
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
+    if not args.no_forms and k == 1 and (args.workload.startswith("poisson3d") or args.workload.startswith("eigen")):
+        line.setdefault("forms", {}).update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
     if not args.no_forms and args.workload == "laplace2d_256":
         line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
     if args.selector and k == 1:
@@ -408,6 +414,22 @@ def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
         forms["split_serial_copy"] = {"gflops": round(tr.flops / t_ser / 1e9, 1), "ms": round(t_ser * 1e3, 4)}
         forms["split_penalty_eq2_model"] = round(pm.split_penalty(A.nnz / A.n_rows), 4)
     return forms
+
+
+def sym_forms(A, torch, spmv, pm, timer, stream, B, C):
+    """Symmetric CRS (Sec. 1.3.1) on the same matrix: the stored triangle, C
+    zeroed and mirrors added atomically; median event time of 200 steps (the
+    zeroing is inside the timed region).  GFlop/s count the full product's
+    flops; hbm_gbs counts the triangle's V_min."""
+    out = {}
+    for f32 in (False, True):
+        with spmv.Plan.from_csr(A, variant=spmv.SPMV_SYM, val_fp32=f32) as p:
+            t = statistics.median(timer.run(lambda: p.apply(B, C, stream), 200, 10)["per_ms"]) / 1e3
+            tr = pm.gpu_sym_min_traffic(A.n_rows, A.nnz, p.info().sym_nnz, val_bytes=4 if f32 else 8)
+            out["sym_fp32val" if f32 else "sym"] = {
+                "gflops": round(tr.flops / t / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t / 1e9, 1),
+                "us": round(t * 1e6, 2), "stored_entries": p.info().sym_nnz}
+    return out
 
 
 def block_precision_forms(A, torch, spmv, pm, stream):

@@ -66,7 +66,13 @@ typedef enum {
   SPMV_CRS_L16 = 6,
   SPMV_CRS_L32 = 7,
   SPMV_SELL = 8,           /* SELL-C-sigma, C = 32, sigma from the options / set_variant         */
-  SPMV_N_VARIANTS = 9
+  SPMV_SYM = 9,            /* symmetric CRS (Sec. 1.3.1): only the entries on and above the      */
+                           /* diagonal are stored and streamed; C is zeroed, then one thread    */
+                           /* per row adds its own sum and, for each stored off-diagonal entry, */
+                           /* the mirror product to the other row, with FP64 atomic adds.       */
+                           /* Square, symmetric matrices only; the order in which a row's       */
+                           /* contributions meet varies from call to call                       */
+  SPMV_N_VARIANTS = 10
 } spmv_variant;
 
 typedef struct {
@@ -91,6 +97,7 @@ typedef struct {
   int32_t tile_nnz;         /* nonzero capacity of one CRS_STAGED tile                          */
   int32_t val_fp32;
   int64_t device_bytes;     /* device memory held by the plan                                   */
+  int64_t sym_nnz;          /* stored entries of the SPMV_SYM triangle (0 if not built)         */
 } spmv_info;
 
 /* Default options: AUTO, sigma 1, FP64 values, max_k 16, no split. */
@@ -154,7 +161,13 @@ spmv_status spmv_apply_host_async(spmv_handle h, const double* B_host, int32_t k
 spmv_status spmv_host_sync(spmv_handle h);
 
 /* Switch the active variant (building its format on first use: the row
- * blocks of CRS_STAGED, or SELL-C-sigma with the given sigma). */
+ * blocks of CRS_STAGED, SELL-C-sigma with the given sigma, or the upper
+ * triangle of SPMV_SYM).  SPMV_SYM needs n_rows == n_cols and a symmetric
+ * matrix: every entry strictly above the diagonal, (i, j, v), matched one to
+ * one by an entry (j, i, v) strictly below it (values compared with
+ * -0.0 == +0.0, so duplicates must mirror one to one); otherwise it returns
+ * SPMV_ERR_UNSUPPORTED, names the first unmatched row, and the active variant
+ * stays as it was. */
 spmv_status spmv_set_variant(spmv_handle h, int32_t variant, int32_t sell_sigma);
 
 spmv_status spmv_get_info(spmv_handle h, spmv_info* info);
@@ -196,6 +209,12 @@ spmv_status spmv_selftest_wait_timeout(int32_t limit_us);
  * Layout: chunks of C = 32 sorted rows, column-major inside a chunk. */
 spmv_status spmv_sell_export(spmv_handle h, int32_t* perm, int64_t* chunk_ptr, int32_t* chunk_len,
                              int32_t* sell_col, double* sell_val);
+
+/* Copy the SPMV_SYM triangle to host arrays sized from spmv_info:
+ * row_ptr[n_rows+1], col[sym_nnz], val[sym_nnz] (any may be NULL).  Row i
+ * holds the entries of row i with col_idx >= i, in their order in the row
+ * (Sec. 1.3.1).  SPMV_ERR_UNSUPPORTED if the triangle was not built. */
+spmv_status spmv_sym_export(spmv_handle h, int32_t* row_ptr, int32_t* col, double* val);
 
 /* Copy the local/halo split arrays to host arrays sized from spmv_info:
  * loc_row_ptr[n_rows+1], loc_col/loc_val[nnz - halo_nnz], halo_rows[n_halo_rows],

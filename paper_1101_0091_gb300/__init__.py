@@ -18,9 +18,10 @@ from ._binding import spmv_apply_host_async, spmv_host_sync, spmv_selftest_wait_
 from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_block, spmv_apply_host,  # noqa: F401
                        spmv_apply_split, spmv_check, spmv_create, spmv_default_options, spmv_destroy,
                        spmv_get_info, spmv_last_error, spmv_options, spmv_sell_export, spmv_set_variant,
-                       spmv_split_export, spmv_features, spmv_set_tuning, spmv_get_tuning, spmv_tuning,
-                       SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
-                       SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_N_VARIANTS)
+                       spmv_split_export, spmv_sym_export, spmv_features, spmv_set_tuning, spmv_get_tuning,
+                       spmv_tuning, SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
+                       SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_SYM,
+                       SPMV_N_VARIANTS)
 
 from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV_BATCH_L1,  # noqa: F401,E402
                              SPMV_BATCH_L2, SPMV_BATCH_L4, SPMV_BATCH_L8, SPMV_BATCH_L32, SPMV_BATCH_N_POLICIES,
@@ -137,6 +138,13 @@ class Plan:
                "sell_val": np.empty(i.sell_slots, np.float64)}
         spmv_sell_export(self.handle, *(out[k].ctypes.data for k in ("perm", "chunk_ptr", "chunk_len", "sell_col",
                                                                      "sell_val")))
+        return out
+
+    def sym_export(self) -> dict:
+        i = self.info()
+        out = {"row_ptr": np.empty(i.n_rows + 1, np.int32), "col": np.empty(i.sym_nnz, np.int32),
+               "val": np.empty(i.sym_nnz, np.float64)}
+        spmv_sym_export(self.handle, *(out[k].ctypes.data for k in ("row_ptr", "col", "val")))
         return out
 
     def split_export(self) -> dict:

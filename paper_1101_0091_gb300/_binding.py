@@ -24,9 +24,10 @@ SPMV_VARIANT_AUTO = 0
 SPMV_CRS_STAGED = 1
 SPMV_CRS_L1, SPMV_CRS_L2, SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32 = 2, 3, 4, 5, 6, 7
 SPMV_SELL = 8
-SPMV_N_VARIANTS = 9
+SPMV_SYM = 9
+SPMV_N_VARIANTS = 10
 VARIANT_NAMES = {1: "crs_staged", 2: "crs_l1", 3: "crs_l2", 4: "crs_l4", 5: "crs_l8", 6: "crs_l16",
-                 7: "crs_l32", 8: "sell"}
+                 7: "crs_l32", 8: "sell", 9: "sym"}
 
 
 class SpmvError(RuntimeError):
@@ -45,7 +46,7 @@ class spmv_info(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("sell_sigma", ctypes.c_int32), ("sell_slots", ctypes.c_int64),
                 ("sell_chunks", ctypes.c_int64), ("n_halo_rows", ctypes.c_int64), ("halo_nnz", ctypes.c_int64),
                 ("n_row_blocks", ctypes.c_int64), ("tile_nnz", ctypes.c_int32), ("val_fp32", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("sym_nnz", ctypes.c_int64)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -63,6 +64,7 @@ _SIGS = {
     "spmv_check": ([_vp, _vp], ctypes.c_int),
     "spmv_sell_export": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_split_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_sym_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_features": ([_i64, _i64, _vp, _vp, _i32, _vp], ctypes.c_int),
 }
 
@@ -150,6 +152,10 @@ def spmv_sell_export(h, perm: int, chunk_ptr: int, chunk_len: int, sell_col: int
 
 def spmv_split_export(h, loc_row_ptr, loc_col, loc_val, halo_rows, halo_row_ptr, halo_col, halo_val) -> None:
     _check(load().spmv_split_export(h, loc_row_ptr, loc_col, loc_val, halo_rows, halo_row_ptr, halo_col, halo_val))
+
+
+def spmv_sym_export(h, row_ptr: int, col: int, val: int) -> None:
+    _check(load().spmv_sym_export(h, row_ptr, col, val))
 
 
 def spmv_features(n_rows: int, n_cols: int, row_ptr: int, col_idx: int, k: int, out: int) -> None:

@@ -96,6 +96,8 @@ struct spmv_plan {
   SellHost sell_host;
   SellDev sell;
   std::vector<void*> sell_ptrs;
+  // symmetric CRS triangle
+  SymDev sym;
   // split
   bool has_split = false;
   SplitHost split_host;
@@ -135,6 +137,7 @@ static void apply_tuning(spmv_plan* p) {
   p->A.prefetch = p->tuning.prefetch_distance;
   p->local.prefetch = p->tuning.prefetch_distance;
   p->sell.prefetch = p->tuning.prefetch_distance;
+  p->sym.prefetch = p->tuning.prefetch_distance;
 }
 
 namespace spmv {
@@ -250,6 +253,35 @@ static spmv_status build_split_dev(spmv_plan* p, int64_t h) {
   return SPMV_OK;
 }
 
+static spmv_status build_sym_dev(spmv_plan* p) {
+  if (p->sym.row_ptr) return SPMV_OK;
+  SymHost S;
+  std::string why;
+  if (!build_sym(p->host, &S, &why)) return fail(SPMV_ERR_UNSUPPORTED, "SYM: " + why);
+  const int64_t nnz = (int64_t)S.col.size();
+  SymDev d;
+  int32_t *drp, *dcol;
+  double* dval;
+  SPMV_CUDA(upload(p->arena, &drp, S.row_ptr.data(), p->host.n_rows + 1, 0));
+  SPMV_CUDA(upload(p->arena, &dcol, S.col.data(), nnz, pad_to(nnz, 4)));
+  SPMV_CUDA(upload(p->arena, &dval, S.val.data(), nnz, pad_to(nnz, 2)));
+  if (p->opt.val_fp32) {
+    std::vector<float> v32(S.val.begin(), S.val.end());  // round to nearest even
+    float* d32;
+    SPMV_CUDA(upload(p->arena, &d32, v32.data(), nnz, pad_to(nnz, 4)));
+    d.val32 = d32;
+    d.val32_special = has_special_f32(v32.data(), nnz);
+  }
+  d.n_rows = p->host.n_rows;
+  d.nnz = nnz;
+  d.row_ptr = drp;
+  d.col = dcol;
+  d.val = dval;
+  d.prefetch = p->tuning.prefetch_distance;
+  p->sym = d;
+  return SPMV_OK;
+}
+
 static spmv_status prepare_variant(spmv_plan* p, int variant, int sigma) {
   if (variant == SPMV_VARIANT_AUTO) variant = SPMV_CRS_L1;
   if (variant < SPMV_CRS_STAGED || variant >= SPMV_N_VARIANTS)
@@ -261,6 +293,10 @@ static spmv_status prepare_variant(spmv_plan* p, int variant, int sigma) {
   }
   if (variant == SPMV_SELL) {
     spmv_status st = build_sell_dev(p, sigma);
+    if (st != SPMV_OK) return st;
+  }
+  if (variant == SPMV_SYM) {
+    spmv_status st = build_sym_dev(p);
     if (st != SPMV_OK) return st;
   }
   p->variant = variant;
@@ -279,6 +315,7 @@ static cudaError_t run_variant(spmv_plan* p, const CsrDev& M, int variant, const
     case SPMV_CRS_L16: return launch_crs_lanes(M, f32, 16, B, ldb, C, ldc, k, s);
     case SPMV_CRS_L32: return launch_crs_lanes(M, f32, 32, B, ldb, C, ldc, k, s);
     case SPMV_SELL: return launch_sell(p->sell, f32, B, ldb, C, ldc, k, s);
+    case SPMV_SYM: return launch_sym(p->sym, f32, B, ldb, C, ldc, k, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -537,6 +574,7 @@ spmv_status spmv_get_info(spmv_handle h, spmv_info* info) {
   info->tile_nnz = h->A.tile;
   info->val_fp32 = h->opt.val_fp32;
   info->device_bytes = h->arena.bytes;
+  info->sym_nnz = h->sym.row_ptr ? h->sym.nnz : 0;
   return SPMV_OK;
 }
 
@@ -567,6 +605,18 @@ spmv_status spmv_sell_export(spmv_handle h, int32_t* perm, int64_t* chunk_ptr, i
     SPMV_CUDA(cudaMemcpy(chunk_len, S.chunk_len, sizeof(int32_t) * (size_t)S.n_chunks, cudaMemcpyDeviceToHost));
   if (sell_col) SPMV_CUDA(cudaMemcpy(sell_col, S.col, sizeof(int32_t) * (size_t)S.slots, cudaMemcpyDeviceToHost));
   if (sell_val) SPMV_CUDA(cudaMemcpy(sell_val, S.val, sizeof(double) * (size_t)S.slots, cudaMemcpyDeviceToHost));
+  return SPMV_OK;
+}
+
+spmv_status spmv_sym_export(spmv_handle h, int32_t* row_ptr, int32_t* col, double* val) {
+  if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
+  if (!h->sym.row_ptr) return fail(SPMV_ERR_UNSUPPORTED, "no SYM triangle built (set_variant SYM first)");
+  DeviceGuard g(h->device);
+  const SymDev& S = h->sym;
+  if (row_ptr)
+    SPMV_CUDA(cudaMemcpy(row_ptr, S.row_ptr, sizeof(int32_t) * (size_t)(S.n_rows + 1), cudaMemcpyDeviceToHost));
+  if (col && S.nnz) SPMV_CUDA(cudaMemcpy(col, S.col, sizeof(int32_t) * (size_t)S.nnz, cudaMemcpyDeviceToHost));
+  if (val && S.nnz) SPMV_CUDA(cudaMemcpy(val, S.val, sizeof(double) * (size_t)S.nnz, cudaMemcpyDeviceToHost));
   return SPMV_OK;
 }
 

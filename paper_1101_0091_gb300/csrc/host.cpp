@@ -183,6 +183,102 @@ void build_split(const HostCsr& A, int64_t h, SplitHost* out) {
   }
 }
 
+// ------------------------------------------------------- symmetric CRS (Sec. 1.3.1)
+// Symmetry test in O(nnz): the strictly-lower entries are transposed into a
+// CRS by a stable counting sort (row j of the transpose lists (i, v) for every
+// stored (i, j) with j < i, in ascending i), then each row's strictly-upper
+// entries are compared with that row of the transpose: directly when they come
+// in the same order (sorted columns), else after sorting both by (column,
+// value key).  Values compare by bit pattern with -0.0 mapped to +0.0.
+static uint64_t sym_value_key(double v) {
+  if (v == 0.0) v = 0.0;
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof(b));
+  return b;
+}
+
+bool build_sym(const HostCsr& A, SymHost* out, std::string* why) {
+  const int64_t n = A.n_rows;
+  if (A.n_cols != n) {
+    *why = "symmetric CRS needs a square matrix";
+    return false;
+  }
+  const int32_t* rp = A.row_ptr.data();
+  const int32_t* col = A.col.data();
+  const double* val = A.val.data();
+  std::vector<int64_t> lt_ptr(n + 1, 0);
+  int64_t n_upper = 0, n_diag = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = rp[i]; j < rp[i + 1]; ++j) {
+      if (col[j] < i) ++lt_ptr[col[j] + 1];
+      else if (col[j] > i) ++n_upper;
+      else ++n_diag;
+    }
+  for (int64_t r = 0; r < n; ++r) lt_ptr[r + 1] += lt_ptr[r];
+  if (lt_ptr[n] != n_upper) {
+    *why = "matrix is not symmetric: " + std::to_string(n_upper) + " entries above the diagonal, " +
+           std::to_string(lt_ptr[n]) + " below";
+    return false;
+  }
+  std::vector<int32_t> lt_col((size_t)n_upper);
+  std::vector<uint64_t> lt_key((size_t)n_upper);
+  {
+    std::vector<int64_t> fill(lt_ptr.begin(), lt_ptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = rp[i]; j < rp[i + 1]; ++j)
+        if (col[j] < i) {
+          const int64_t q = fill[col[j]]++;
+          lt_col[q] = (int32_t)i;
+          lt_key[q] = sym_value_key(val[j]);
+        }
+  }
+  std::vector<std::pair<int32_t, uint64_t>> a, b;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t q = lt_ptr[i], cnt = 0;
+    bool in_order = true;
+    for (int64_t j = rp[i]; j < rp[i + 1]; ++j) {
+      if (col[j] <= i) continue;
+      ++cnt;
+      if (in_order && (q >= lt_ptr[i + 1] || lt_col[q] != col[j] || lt_key[q] != sym_value_key(val[j])))
+        in_order = false;
+      ++q;
+    }
+    if (cnt != lt_ptr[i + 1] - lt_ptr[i]) {
+      *why = "matrix is not symmetric: row " + std::to_string(i) + " has " + std::to_string(cnt) +
+             " entries above the diagonal, column " + std::to_string(i) + " has " +
+             std::to_string(lt_ptr[i + 1] - lt_ptr[i]) + " below";
+      return false;
+    }
+    if (in_order) continue;
+    a.clear();
+    b.clear();
+    for (int64_t j = rp[i]; j < rp[i + 1]; ++j)
+      if (col[j] > i) a.emplace_back(col[j], sym_value_key(val[j]));
+    for (int64_t t = lt_ptr[i]; t < lt_ptr[i + 1]; ++t) b.emplace_back(lt_col[t], lt_key[t]);
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a != b) {
+      *why = "matrix is not symmetric: the entries above the diagonal in row " + std::to_string(i) +
+             " do not mirror those below it in column " + std::to_string(i);
+      return false;
+    }
+  }
+  out->row_ptr.assign(n + 1, 0);
+  out->col.resize((size_t)(n_upper + n_diag));
+  out->val.resize((size_t)(n_upper + n_diag));
+  int64_t p = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = rp[i]; j < rp[i + 1]; ++j)
+      if (col[j] >= i) {
+        out->col[p] = col[j];
+        out->val[p++] = val[j];
+      }
+    out->row_ptr[i + 1] = (int32_t)p;
+  }
+  return true;
+}
+
+
 // Feature vector of the cost model (34 entries); definition in the header of
 // spmv_features in include/spmv.h.
 void compute_features(int64_t n, int64_t n_cols, const int32_t* rp, const int32_t* col, int k, double* f) {

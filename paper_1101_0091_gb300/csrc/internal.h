@@ -37,12 +37,7 @@ constexpr int kSellC = 32;           // SELL chunk height
 constexpr uint32_t kBlockWarpFlag = 0x80000000u;  // high bit of a row-block entry: warp-per-row block
 constexpr int kDefaultPrefetch = 152;  // default L2 prefetch distance (CTAs ahead; one per SM)
 
-// ------------------------------------------------------- device buffers
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
+// ------------------------------------------------------- host copies of the formats
 struct HostCsr {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   std::vector<int32_t> row_ptr, col;
@@ -53,6 +48,12 @@ struct SellHost {
   int64_t C = kSellC, sigma = 1, n_chunks = 0, slots = 0;
   std::vector<int32_t> perm, chunk_len, col;
   std::vector<int64_t> chunk_ptr;
+  std::vector<double> val;
+};
+
+// Symmetric CRS (Sec. 1.3.1): the entries of each row with col >= row, in their order in the row.
+struct SymHost {
+  std::vector<int32_t> row_ptr, col;
   std::vector<double> val;
 };
 
@@ -92,6 +93,17 @@ struct SellDev {
   bool val32_special = false;
 };
 
+// Stored triangle of SPMV_SYM.
+struct SymDev {
+  int64_t n_rows = 0, nnz = 0;
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;     // padded like CsrDev::col
+  const double* val = nullptr;
+  const float* val32 = nullptr;
+  int prefetch = 0;
+  bool val32_special = false;
+};
+
 // Halo part of a split: rows listed in `rows`, CRS over them.
 struct HaloDev {
   int64_t n_rows = 0, nnz = 0;
@@ -117,6 +129,8 @@ std::vector<uint32_t> build_row_blocks(const int32_t* row_ptr, int64_t n_rows, i
                                        int long_row, int* tile_out);
 void build_sell(const HostCsr& A, int64_t C, int64_t sigma, SellHost* out);
 void build_split(const HostCsr& A, int64_t h, SplitHost* out);
+// False (reason in *why) unless A is square and symmetric in the sense of spmv_set_variant.
+bool build_sym(const HostCsr& A, SymHost* out, std::string* why);
 void compute_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
                       int k, double* f);
 
@@ -130,6 +144,8 @@ cudaError_t launch_sell(const SellDev& S, bool fp32, const double* B, int64_t ld
                         int64_t ldc, int k, cudaStream_t s);
 cudaError_t launch_halo(const HaloDev& H, bool fp32, const double* B, int64_t ldb, double* C,
                         int64_t ldc, int k, cudaStream_t s);
-cudaError_t launch_zero_rows(double* C, int64_t n_rows, int64_t ldc, int k, cudaStream_t s);
+// Zeroes C[:, 0:k] on the stream, then runs the symmetric kernel.
+cudaError_t launch_sym(const SymDev& S, bool fp32, const double* B, int64_t ldb, double* C, int64_t ldc,
+                       int k, cudaStream_t s);
 
 }  // namespace spmv

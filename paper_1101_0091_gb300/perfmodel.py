@@ -75,6 +75,14 @@ def gpu_min_traffic(n_rows: int, n_cols: int, nnz: int, k: int = 1, val_bytes: i
     return Traffic(int(b), int(2 * k * nnz))
 
 
+def gpu_sym_min_traffic(n: int, nnz: int, nnz_upper: int, k: int = 1, val_bytes: int = 8) -> Traffic:
+    """V_min of the symmetric CRS product (Sec. 1.3.1) of a square matrix: the
+    stored triangle (nnz_upper entries on or above the diagonal) is read once,
+    B read once and C written once.  The flops are those of the full product."""
+    b = nnz_upper * (val_bytes + 4) + 4 * (n + 1) + 8 * k * n + 8 * k * n
+    return Traffic(int(b), int(2 * k * nnz))
+
+
 def gpu_split_extra_bytes(n_halo_rows: int, k: int = 1) -> int:
     """Extra DRAM bytes of the split: the halo pass re-reads and re-writes C on
     halo rows (16k B each), plus the halo row list and its row pointers (8 B)."""

@@ -101,6 +101,42 @@ def test_eigen_full_staged_and_sell(lib):
             check_sampled(host(C), A, B, rows)
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_poisson280_symmetric(lib, poisson280, fp32):
+    """Symmetric CRS on the full 3D Poisson workload: sampled rows of the product
+    against the oracle's CRS loop over the full rows; A * 1 = 1e-3 in every row."""
+    import torch
+    A = poisson280
+    B = gen.uniform(A.n_cols, seed=0)
+    rows = sample_rows(A.n_rows, 4, count=10_000)
+    with lib.Plan.from_csr(A, variant=lib.SPMV_SYM, val_fp32=fp32) as p:
+        assert p.info().sym_nnz == (A.nnz + A.n_rows) // 2
+        C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply(dev(B), C)
+        y = host(C)
+        assert not np.isnan(y).any()
+        check_sampled(y, A, B, rows, f32val=fp32)
+        if not fp32:
+            ones = np.ones(A.n_cols)
+            p.apply(dev(ones), C)
+            y1 = host(C)
+            S = sub_csr(A, rows)
+            assert np.all(np.abs(y1[rows] - 1e-3) <= TOL_FP64 * oracle.abs_scale(S, ones))
+
+
+def test_eigen_full_symmetric(lib):
+    import torch
+    A = gen.eigen_shaped()
+    B = gen.uniform(A.n_cols, seed=0)
+    rows = sample_rows(A.n_rows, 5)
+    with lib.Plan.from_csr(A, variant=lib.SPMV_SYM) as p:
+        C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply(dev(B), C)
+        y = host(C)
+        assert not np.isnan(y).any()
+        check_sampled(y, A, B, rows)
+
+
 def test_batch512_full_size_sampled(lib):
     """The 512-member uneven batch, k = 4, in the configuration the benchmark
     times (sorted policy, autotuned, graph replay), on 40 sampled rows per

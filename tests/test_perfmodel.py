@@ -60,3 +60,18 @@ def test_gpu_min_traffic():
     n, nnz = 1000, 7000
     assert pm.gpu_code_balance(7.0) == pytest.approx(pm.gpu_min_traffic(n, n, nnz).bytes_min / (2 * nnz), rel=1e-3)
     assert pm.kappa_gpu(1.1e9, 1.0e9, 10 ** 8) == pytest.approx(1.0)
+
+
+def test_sym_traffic_halves_the_matrix_stream():
+    """Symmetric storage keeps (nnz + n) / 2 entries: the val/col part of V_min
+    tends to one half of CRS's as Nnzr grows (Sec. 1.3.1), and the
+    flops stay those of the full product."""
+    n = 1000
+    for nnzr in (7, 15, 101):
+        nnz = n * nnzr
+        full = pm.gpu_min_traffic(n, n, nnz)
+        sym = pm.gpu_sym_min_traffic(n, nnz, (nnz + n) // 2)
+        assert sym.flops == full.flops
+        rest = 4 * (n + 1) + 16 * n
+        ratio = (sym.bytes_min - rest) / (full.bytes_min - rest)
+        assert ratio == pytest.approx((nnzr + 1) / (2 * nnzr))
