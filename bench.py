@@ -369,6 +369,10 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
     if not args.no_forms and k == 1 and (args.workload.startswith("poisson3d") or args.workload.startswith("eigen")):
         line.setdefault("forms", {}).update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
+    if not args.no_forms and k == 1 and args.workload.startswith("poisson3d"):
+        line["solver"] = cg_forms(A, torch, spmv, pm, stream)
+    if not args.no_forms and k == 1 and args.workload.startswith("eigen"):
+        line["solver"] = lanczos_forms(A, torch, spmv, pm, stream)
     if not args.no_forms and args.workload == "laplace2d_256":
         line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
     if args.selector and k == 1:
@@ -429,6 +433,91 @@ def sym_forms(A, torch, spmv, pm, timer, stream, B, C):
             out["sym_fp32val" if f32 else "sym"] = {
                 "gflops": round(tr.flops / t / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t / 1e9, 1),
                 "us": round(t * 1e6, 2), "stored_entries": p.info().sym_nnz}
+    return out
+
+
+def cg_bytes_per_iteration(pm, A, k: int) -> int:
+    """Algorithmic bytes of one CG iteration of the library: the SpMM's V_min
+    (P read, Q written) + alpha (read P, Q) + update (read X, P, R, Q; write
+    X, R) + direction (read R, P; write P): V_min + 88 k n bytes."""
+    return pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k).bytes_min + 88 * k * A.n_rows
+
+
+def cg_forms(A, torch, spmv, pm, stream, iters: int = 50):
+    """Conjugate gradients on k columns through the default plan, a fixed
+    number of iterations (rtol = 0), polled once: time per iteration, the
+    solver's flop rate (SpMM + 10 k n vector flops per iteration) and its
+    algorithmic bytes against the measured copy peak."""
+    import gen
+    hbm, hbm_kind = measured_hbm()
+    out = {"method": "CG (Hestenes-Stiefel), k independent columns, graph-replayed iterations",
+           "iterations": iters,
+           "bound": "SpMM at max(HBM, FP64-pipe) time of its V_min and 2k nnz flops, plus the vector "
+                    "kernels' 88 k n bytes at the measured copy peak (the kernels run one after another)"}
+    for k in (1, 4, 8):
+        # k = 1 is HBM-bound (CRS_L1); k >= 2 is FP64-pipe-bound, where CRS_STAGED issues fewest extra ops
+        variant = spmv.SPMV_CRS_L1 if k == 1 else spmv.SPMV_CRS_STAGED
+        with spmv.Plan.from_csr(A, variant=variant) as p:
+            B = torch.from_numpy(gen.rhs_block(A.n_cols, k, seed=0)).cuda()
+            X = torch.zeros_like(B)
+            stream.wait_stream(torch.cuda.current_stream())
+            with spmv.Solver(p, k) as s:
+                s.cg(B, X, max_iter=3, rtol=0.0, check_every=iters, stream=stream)  # warm-up
+                ts = []
+                for _ in range(3):
+                    X.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    it, rr, summ = s.cg(B, X, max_iter=iters, rtol=0.0, check_every=iters, stream=stream)
+                    ts.append(time.perf_counter() - t0)
+        t_it = min(ts) / iters
+        flops = 2 * k * A.nnz + 10 * k * A.n_rows
+        byts = cg_bytes_per_iteration(pm, A, k)
+        spmm = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
+        t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (FP64_PEAK_GFLOPS * 1e9))
+                   + 88 * k * A.n_rows / (hbm * 1e9))
+        out[f"k{k}"] = {"plan_variant": "crs_l1" if k == 1 else "crs_staged",
+                        "us_per_iteration": round(t_it * 1e6, 1), "gflops": round(flops / t_it / 1e9, 1),
+                        "hbm_gbs": round(byts / t_it / 1e9, 1), "bytes_per_iteration": byts,
+                        "bound_us": round(t_bound * 1e6, 1), "frac_of_bound": round(t_bound / t_it, 4),
+                        "column_iterations_per_s": round(k / t_it, 1)}
+    out["hbm_peak"] = hbm
+    out["fp64_peak_gflops"] = round(FP64_PEAK_GFLOPS, 1)
+    out["timing"] = "host wall clock around the synchronous solve (one poll at the end), best of 3"
+    return out
+
+
+def lanczos_forms(A, torch, spmv, pm, stream, m: int = 30):
+    """Lanczos (no reorthogonalisation) on k start vectors through the
+    selector's SELL-32-4096 plan: time per step.  Bytes per step: V_min(k) +
+    alpha (read W, v, v_prev; write W) + beta (read W, v; write W) + scale
+    (read W; write v) = V_min + 72 k n."""
+    import gen
+    hbm, _ = measured_hbm()
+    out = {"method": "Lanczos three-term recurrence, k independent start vectors", "steps": m}
+    with spmv.Plan.from_csr(A, variant=spmv.SPMV_SELL, sell_sigma=4096) as p:
+        for k in (1, 4):
+            V0 = torch.from_numpy(gen.rhs_block(A.n_cols, k, seed=0)).cuda()
+            stream.wait_stream(torch.cuda.current_stream())
+            with spmv.Solver(p, k) as s:
+                s.lanczos(V0, 3, stream=stream)
+                ts = []
+                for _ in range(3):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    s.lanczos(V0, m, stream=stream)
+                    ts.append(time.perf_counter() - t0)
+            t_it = min(ts) / m
+            spmm = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
+            byts = spmm.bytes_min + 72 * k * A.n_rows
+            t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (FP64_PEAK_GFLOPS * 1e9))
+                       + 72 * k * A.n_rows / (hbm * 1e9))
+            out[f"k{k}"] = {"us_per_step": round(t_it * 1e6, 1),
+                            "gflops": round((2 * k * A.nnz + 8 * k * A.n_rows) / t_it / 1e9, 1),
+                            "hbm_gbs": round(byts / t_it / 1e9, 1), "bound_us": round(t_bound * 1e6, 1),
+                            "frac_of_bound": round(t_bound / t_it, 4)}
+    out["note"] = ("the random gathers of this matrix make its SpMM L2-bound (SELL-32-4096 reaches about "
+                   "0.55 of the copy peak alone), so the HBM/FP64 bound is not reachable here")
     return out
 
 

@@ -379,6 +379,57 @@ spmv_status spmv_model_load(spmv_model_handle* out, const char* path);
 spmv_status spmv_model_destroy(spmv_model_handle m);
 
 /* ----------------------------------------------------------------------------
+ * Iterative consumers of the product.  Sec. 1.3.1 names Lanczos and
+ * Jacobi-Davidson as the eigensolvers run on the Hamiltonian matrices, whose
+ * run time the product dominates; conjugate gradients is the matching solver
+ * for symmetric positive definite matrices such as the Poisson workload.
+ * Both run on k independent columns, so each iteration's product is one
+ * k-column spmv_apply_block through the plan (whatever its variant).
+ *
+ * A solver holds three n x k work blocks and per-column scalars on the
+ * plan's device; it borrows the plan (destroy the solver first).  Vector
+ * blocks are row-major n x k with ld = k (X[i*k + c]) and 16-byte aligned
+ * (else SPMV_ERR_ARG).  Inner products are reduced in a fixed order: repeated
+ * solves give identical results.
+ * ------------------------------------------------------------------------- */
+typedef struct spmv_solver* spmv_solver_handle;
+
+typedef struct {
+  int32_t iterations;   /* largest number of iterations run by a column               */
+  int32_t converged;    /* columns with |r| <= rtol |b|                                */
+  int32_t breakdown;    /* columns stopped because p.Ap <= 0 (A not positive definite) */
+  int32_t reserved;
+} spmv_cg_summary;
+
+/* Square plans only; 1 <= k <= the plan's max_k. */
+spmv_status spmv_solver_create(spmv_handle A, int32_t k, spmv_solver_handle* out);
+/* Synchronises the device, frees the work blocks; NULL is accepted. */
+spmv_status spmv_solver_destroy(spmv_solver_handle s);
+
+/* Conjugate gradients (Hestenes-Stiefel) on the k columns of B_dev.  X_dev
+ * holds the initial guess on entry and the iterate on return.  Per column:
+ * R = B - A X, P = R; each iteration Q = A P, alpha = R.R / P.Q, X += alpha P,
+ * R -= alpha Q, beta = R.R(new) / R.R(old), P = R + beta P.  A column stops
+ * (exactly as it is) once |R| <= rtol |B|, or on breakdown (P.Q <= 0); the
+ * call returns when every column has stopped or after max_iter iterations.
+ * The host polls the device every check_every iterations (those iterations
+ * run from a CUDA graph captured on first use for these B, X and check_every).
+ * iterations_host[k] and rr_host[k] (final R.R) may be NULL.  Synchronous. */
+spmv_status spmv_cg_solve(spmv_solver_handle s, const double* B_dev, double* X_dev, int32_t max_iter,
+                          double rtol, int32_t check_every, void* stream, int32_t* iterations_host,
+                          double* rr_host, spmv_cg_summary* summary);
+
+/* m steps of the Lanczos three-term recurrence (no reorthogonalisation) from
+ * the k columns of V0_dev: v_1 = v0/|v0|; w = A v_j - beta_{j-1} v_{j-1};
+ * alpha_j = w.v_j; w -= alpha_j v_j; beta_j = |w|; v_{j+1} = w / beta_j.  A
+ * column whose beta reaches 0 stops (zeros from there on).  alpha_host and
+ * beta_host are m x k row-major host arrays; the Ritz values are the
+ * eigenvalues of the tridiagonal matrix with alpha_1..m on the diagonal and
+ * beta_1..m-1 beside it.  Synchronous. */
+spmv_status spmv_lanczos(spmv_solver_handle s, const double* V0_dev, int32_t m, double* alpha_host,
+                         double* beta_host, void* stream);
+
+/* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).
  * out[34] (float64) for HOST CRS arrays and k right-hand sides:
  *   [0:13]  fraction of rows in length bin b: b(L) = 0 for L = 0, else

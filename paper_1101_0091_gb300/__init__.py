@@ -32,6 +32,8 @@ from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV
                              spmv_batch_get_config, spmv_batch_info, spmv_batch_set_config, spmv_batch_set_io,
                              spmv_batch_set_policies)
 
+from ._binding_solver import (Solver, spmv_cg_solve, spmv_cg_summary, spmv_lanczos,  # noqa: F401,E402
+                             spmv_solver_create, spmv_solver_destroy)
 from ._binding_model import (spmv_model_adam_step, spmv_model_create, spmv_model_destroy,  # noqa: F401,E402
                              spmv_model_forward, spmv_model_get_params, spmv_model_info, spmv_model_load,
                              spmv_model_loss_grad, spmv_model_save, spmv_model_select, spmv_model_set_normalizer,

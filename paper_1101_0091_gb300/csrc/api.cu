@@ -146,6 +146,7 @@ const int32_t* plan_host_row_ptr(spmv_handle h) { return h->host.row_ptr.data();
 const int32_t* plan_host_col(spmv_handle h) { return h->host.col.data(); }
 const double* plan_host_val(spmv_handle h) { return h->host.val.data(); }
 int plan_device(spmv_handle h) { return h->device; }
+int plan_max_k(spmv_handle h) { return h->opt.max_k; }
 }  // namespace spmv
 
 static spmv_status build_blocks(spmv_plan* p, CsrDev* M, const int32_t* host_row_ptr) {
