@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison of forms")
+    ap.add_argument("--forms", default="all",
+                    help="comma list of form groups to run: variants, sym, spmm, solver, ordering, block (or all)")
+    ap.add_argument("--form-steps", type=int, default=100, help="timed steps per kernel in the ordering forms")
     ap.add_argument("--selector", action="store_true",
                     help="train the cost model on generated matrices (seeds >= 1000) and report its choice, "
                          "its regret against the exhaustive sweep and its gain over the default")
@@ -109,11 +112,11 @@ def kernel_fingerprint(files) -> str:
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"crs_l1": ["k_lanes.cu", "device.cuh", "internal.h"],
-                  "crs_staged": ["k_staged.cu", "device.cuh", "internal.h"],
-                  "sell": ["k_sell.cu", "device.cuh", "internal.h"],
-                  "sym": ["k_sym.cu", "device.cuh", "internal.h"],
-                  "batch": ["batch_kernel.cuh", "batch.cu", "device.cuh", "internal.h"]}
+KERNEL_SOURCES = {"crs_l1": ["k_lanes.cu", "device.cuh", "layout.h"],
+                  "crs_staged": ["k_staged.cu", "device.cuh", "layout.h"],
+                  "sell": ["k_sell.cu", "device.cuh", "layout.h"],
+                  "sym": ["k_sym.cu", "device.cuh", "layout.h"],
+                  "batch": ["batch_kernel.cuh", "batch.cu", "device.cuh", "layout.h"]}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -365,15 +368,22 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
                        "h2d_bytes_per_step": 8 * A.n_cols * k, "d2h_bytes_per_step": 8 * A.n_rows * k,
                        "api": "spmv_apply_host_async, pipelined, host_sync at the end",
                        "synchronous_call_gflops": round(tr.flops * world / sync_t / 1e9, 3)}
-    if not args.no_forms and args.workload.startswith("poisson3d"):
+    groups = set() if args.no_forms else (
+        {"variants", "sym", "spmm", "solver", "ordering", "block"} if args.forms == "all" else set(args.forms.split(",")))
+    poisson, eigen = args.workload.startswith("poisson3d"), args.workload.startswith("eigen")
+    if "variants" in groups and poisson:
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
-    if not args.no_forms and k == 1 and (args.workload.startswith("poisson3d") or args.workload.startswith("eigen")):
+    if "sym" in groups and k == 1 and (poisson or eigen):
         line.setdefault("forms", {}).update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
-    if not args.no_forms and k == 1 and args.workload.startswith("poisson3d"):
+    if "spmm" in groups and k == 1 and poisson:
+        line["spmm"] = spmm_forms(A, torch, spmv, pm, timer, stream)
+    if "solver" in groups and k == 1 and poisson:
         line["solver"] = cg_forms(A, torch, spmv, pm, stream)
-    if not args.no_forms and k == 1 and args.workload.startswith("eigen"):
+    if "solver" in groups and k == 1 and eigen:
         line["solver"] = lanczos_forms(A, torch, spmv, pm, stream)
-    if not args.no_forms and args.workload == "laplace2d_256":
+    if "ordering" in groups and k == 1 and eigen:
+        line["ordering"] = ordering_forms(A, torch, spmv, pm, timer, stream, B, C, args.workload, args.form_steps)
+    if "block" in groups and args.workload == "laplace2d_256":
         line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
     if args.selector and k == 1:
         line["selector"] = plan_selector(args, A, timer, stream, tr, spmv)
@@ -433,6 +443,79 @@ def sym_forms(A, torch, spmv, pm, timer, stream, B, C):
             out["sym_fp32val" if f32 else "sym"] = {
                 "gflops": round(tr.flops / t / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t / 1e9, 1),
                 "us": round(t * 1e6, 2), "stored_entries": p.info().sym_nnz}
+    return out
+
+
+def spmm_forms(A, torch, spmv, pm, timer, stream):
+    """k right-hand sides on the full matrix (a11): median event time per
+    product for three kernels.  Each nonzero needs k FP64 FMAs, so for k >= 2
+    the bound is the FP64 pipe (2k nnz flops at 1258.6 GFLOP/s), not HBM."""
+    import gen
+    hbm, _ = measured_hbm()
+    out = {"bound": "max(V_min(k) / measured copy peak, 2 k nnz / FP64 peak)"}
+    with spmv.Plan.from_csr(A) as p:
+        for k in (2, 4, 8, 16):
+            B = torch.from_numpy(gen.rhs_block(A.n_cols, k, seed=0)).cuda()
+            C = torch.empty_like(B)
+            stream.wait_stream(torch.cuda.current_stream())
+            tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
+            t_bound = max(tr.bytes_min / (hbm * 1e9), tr.flops / (FP64_PEAK_GFLOPS * 1e9))
+            row = {"bound_us": round(t_bound * 1e6, 1)}
+            for name in ("crs_l1", "crs_staged", "sell_s256"):
+                vid, sigma = VARIANTS[name]
+                p.set_variant(vid, sigma)
+                t = statistics.median(timer.run(lambda: p.apply_block(B, C, k, stream), 30, 3)["per_ms"]) / 1e3
+                row[name] = {"us": round(t * 1e6, 1), "gflops": round(tr.flops / t / 1e9, 1),
+                             "fp64_frac": round(tr.flops / t / 1e9 / FP64_PEAK_GFLOPS, 4),
+                             "frac_of_bound": round(t_bound / t, 4)}
+            out[f"k{k}"] = row
+            del B, C
+    return out
+
+
+def ordering_forms(A, torch, spmv, pm, timer, stream, B, C, workload, steps=100):
+    """The same matrix in three numberings (Sec. 1.3.1): as generated (the
+    HMeP-like numbering), renumbered by the 400 x 15,504 Kronecker transpose
+    (HMEp-like) and reordered by RCM.  Per numbering: bandwidth, mean |i - j|,
+    and median event times of SELL-32-4096 and CRS_L1; for RCM also the host
+    time of the permutation and the device time of moving B in and C out.
+    kappa_gpu = (DRAM bytes - V_min) / nnz where an ncu capture of that
+    numbering is recorded in profiles/traffic.json."""
+    import gen
+    tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz)
+    rows = np.repeat(np.arange(A.n_rows, dtype=np.int64), np.diff(A.row_ptr))
+    out = {}
+    t0 = time.perf_counter()
+    rcm_perm = spmv.rcm(A.n_rows, A.row_ptr, A.col_idx)
+    t_rcm = time.perf_counter() - t0
+    orders = [("natural", None), ("kronecker_transposed", gen.kronecker_transpose(400, A.n_rows // 400)),
+              ("rcm", rcm_perm)]
+    for name, perm in orders:
+        if perm is None:
+            rp, ci, va = A.row_ptr, A.col_idx, A.val
+        else:
+            rp, ci, va = spmv.permute_csr(A.n_rows, A.row_ptr, A.col_idx, A.val, perm)
+        d = np.abs(rows - ci.astype(np.int64))
+        row = {"bandwidth": int(d.max()), "mean_abs_i_minus_j": round(float(d.mean()), 1)}
+        with spmv.Plan(A.n_rows, A.n_cols, rp, ci, va, variant=spmv.SPMV_SELL, sell_sigma=4096) as p:
+            for vname, vid, sigma in (("sell_s4096", spmv.SPMV_SELL, 4096), ("crs_l1", spmv.SPMV_CRS_L1, 1)):
+                p.set_variant(vid, sigma)
+                t = statistics.median(timer.run(lambda: p.apply(B, C, stream), steps, 3)["per_ms"]) / 1e3
+                key = ("sell" if vname.startswith("sell") else vname)
+                dram = ncu_traffic(key, f"{workload}:{name}")
+                row[vname] = {"us": round(t * 1e6, 1), "gflops": round(tr.flops / t / 1e9, 1),
+                              "hbm_gbs": round(tr.bytes_min / t / 1e9, 1),
+                              "kappa_gpu": (round(pm.kappa_gpu(dram, tr.bytes_min, A.nnz), 3)
+                                            if dram is not None else None)}
+        if perm is not None and name == "rcm":
+            with spmv.Reorder(perm) as r:
+                Bp, Cp = torch.empty_like(B), torch.empty_like(C)
+                t_g = statistics.median(timer.run(lambda: r.gather(B, Bp, stream), steps, 3)["per_ms"]) / 1e3
+                t_s = statistics.median(timer.run(lambda: r.scatter(Cp, C, stream), steps, 3)["per_ms"]) / 1e3
+            row["host_rcm_s"] = round(t_rcm, 2)
+            row["gather_B_us"] = round(t_g * 1e6, 1)
+            row["scatter_C_us"] = round(t_s * 1e6, 1)
+        out[name] = row
     return out
 
 

@@ -222,3 +222,13 @@ def symmetric_from(A: CSR, seed: int = 0, shuffle: bool = False) -> CSR:
     rp = np.zeros(n + 1, dtype=np.int32)
     rp[1:] = np.cumsum(np.bincount(R, minlength=n))
     return CSR(n, n, rp, Cc[order].astype(np.int32), V[order])
+
+
+def kronecker_transpose(n1: int = 400, n2: int = 15_504) -> np.ndarray:
+    """Renumbering of an n1 x n2 product basis from index e*n2 + p (the second
+    factor contiguous) to p*n1 + e (the first factor contiguous), as a
+    permutation perm[new] = old: perm[p*n1 + e] = e*n2 + p.  Sec. 1.3.1's two
+    numberings of the Hamiltonian basis differ in exactly this way."""
+    e = np.arange(n1, dtype=np.int64)
+    p = np.arange(n2, dtype=np.int64)
+    return (e[None, :] * n2 + p[:, None]).reshape(-1).astype(np.int32)

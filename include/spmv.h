@@ -430,6 +430,45 @@ spmv_status spmv_lanczos(spmv_solver_handle s, const double* V0_dev, int32_t m, 
                          double* beta_host, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * Reordering.  Sec. 1.3.1 applies reverse Cuthill-McKee (RCM) to the
+ * Hamiltonian matrix to make the accesses to B more local.  The permutation
+ * is computed on the host with fixed tie-breaking (unique result):
+ *  - graph: the pattern of A + A^T without self loops; degree = number of
+ *    distinct neighbours;
+ *  - components in order of their smallest node; each starts at a
+ *    pseudo-peripheral node: r = the node of minimum (degree, index), then
+ *    repeatedly the node of minimum (degree, index) in the last level of r's
+ *    breadth-first level structure replaces r while its structure is deeper;
+ *  - Cuthill-McKee breadth-first order from r, each node appending its
+ *    unvisited neighbours in ascending (degree, index); perm is the reverse
+ *    of that order (perm[new] = old).
+ * ------------------------------------------------------------------------- */
+typedef struct spmv_reorder* spmv_reorder_handle;
+
+/* RCM permutation of a square HOST CRS pattern (n x n): perm[n] (host). */
+spmv_status spmv_rcm(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* perm);
+
+/* A' = P A P^T for perm[new] = old (host arrays): row r of A' is row perm[r]
+ * of A with every column c relabelled to inv[c] (inv[perm[r]] = r) and the
+ * entries sorted by the new column (stable: duplicates keep their order).
+ * out_row_ptr[n+1], out_col_idx / out_val [nnz].  perm must be a permutation
+ * of 0..n-1 (else SPMV_ERR_ARG). */
+spmv_status spmv_permute_csr(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                             const int32_t* perm, int32_t* out_row_ptr, int32_t* out_col_idx, double* out_val);
+
+/* A validated permutation on the current device, to move k-column row-major
+ * blocks between the original and the permuted row order:
+ *   gather:  Y[r*ldy + c] = X[perm[r]*ldx + c]   (original -> permuted order)
+ *   scatter: Y[perm[r]*ldy + c] = X[r*ldx + c]   (permuted -> original order)
+ * for r < n, c < k; X and Y are distinct device blocks; asynchronous. */
+spmv_status spmv_reorder_create(int64_t n, const int32_t* perm, spmv_reorder_handle* out);
+spmv_status spmv_reorder_gather(spmv_reorder_handle h, int32_t k, const double* X_dev, int64_t ldx, double* Y_dev,
+                                int64_t ldy, void* stream);
+spmv_status spmv_reorder_scatter(spmv_reorder_handle h, int32_t k, const double* X_dev, int64_t ldx, double* Y_dev,
+                                 int64_t ldy, void* stream);
+spmv_status spmv_reorder_destroy(spmv_reorder_handle h);
+
+/* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).
  * out[34] (float64) for HOST CRS arrays and k right-hand sides:
  *   [0:13]  fraction of rows in length bin b: b(L) = 0 for L = 0, else

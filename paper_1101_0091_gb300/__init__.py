@@ -32,6 +32,7 @@ from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV
                              spmv_batch_get_config, spmv_batch_info, spmv_batch_set_config, spmv_batch_set_io,
                              spmv_batch_set_policies)
 
+from ._binding_reorder import Reorder, permute_csr, rcm  # noqa: F401,E402
 from ._binding_solver import (Solver, spmv_cg_solve, spmv_cg_summary, spmv_lanczos,  # noqa: F401,E402
                              spmv_solver_create, spmv_solver_destroy)
 from ._binding_model import (spmv_model_adam_step, spmv_model_create, spmv_model_destroy,  # noqa: F401,E402

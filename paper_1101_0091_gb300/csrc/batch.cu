@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "batch_kernel.cuh"
+#include "internal.h"
 
 namespace spmv {
 

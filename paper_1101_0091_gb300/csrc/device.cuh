@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "internal.h"
+#include "layout.h"
 
 namespace spmv {
 

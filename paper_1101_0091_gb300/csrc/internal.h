@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/spmv.h"
+#include "layout.h"
 
 namespace spmv {
 
@@ -21,21 +22,6 @@ spmv_status cuda_fail(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                                              \
     if (e_ != cudaSuccess) return ::spmv::cuda_fail(e_, #call);           \
   } while (0)
-
-// Device status word codes written by kernels (0 = fine).
-enum : int { DEV_OK = 0, DEV_WAIT_TIMEOUT = 1 };
-
-// Bounded device waits give up after this many nanoseconds of %globaltimer.
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;
-
-// ------------------------------------------------------- layout constants
-constexpr int kThreads = 256;        // threads per CTA of the row kernels
-constexpr int kStagedRows = 256;     // rows per CRS_STAGED block (one per thread)
-constexpr int kLongRow = 64;         // rows longer than this are handled warp-per-row
-constexpr int kWarpRowsPerBlock = kThreads / 32;
-constexpr int kSellC = 32;           // SELL chunk height
-constexpr uint32_t kBlockWarpFlag = 0x80000000u;  // high bit of a row-block entry: warp-per-row block
-constexpr int kDefaultPrefetch = 152;  // default L2 prefetch distance (CTAs ahead; one per SM)
 
 // ------------------------------------------------------- host copies of the formats
 struct HostCsr {
@@ -63,57 +49,8 @@ struct SplitHost {
   std::vector<double> loc_val, halo_val;
 };
 
-// Device view of one CRS matrix (values in FP64 and, optionally, FP32).
-struct CsrDev {
-  int64_t n_rows = 0, n_cols = 0, nnz = 0;
-  const int32_t* row_ptr = nullptr;
-  const int32_t* col = nullptr;     // padded to a multiple of 4 entries + 4
-  const double* val = nullptr;      // padded to a multiple of 2 entries + 2
-  const float* val32 = nullptr;     // padded to a multiple of 4 entries + 4
-  const uint32_t* blk = nullptr;    // row blocks of CRS_STAGED (n_blk + 1 entries)
-  int64_t n_blk = 0;
-  int tile = 0;                     // nonzero capacity of a CRS_STAGED tile
-  int prefetch = 0;                 // CTAs ahead whose val/col slices are prefetched into L2 (0 = off)
-  bool val32_special = false;       // val32 holds a subnormal, infinite or NaN float
-};
-
 // True if any float is subnormal, infinite or NaN (zero and normals are "plain").
 bool has_special_f32(const float* v, int64_t n);
-
-struct SellDev {
-  int64_t n_rows = 0, n_chunks = 0, slots = 0;
-  int sigma = 0;
-  const int32_t* perm = nullptr;
-  const int64_t* chunk_ptr = nullptr;
-  const int32_t* chunk_len = nullptr;
-  const int32_t* col = nullptr;
-  const double* val = nullptr;
-  const float* val32 = nullptr;
-  int prefetch = 0;                 // CTAs ahead whose slots are prefetched into L2 (0 = off)
-  bool val32_special = false;
-};
-
-// Stored triangle of SPMV_SYM.
-struct SymDev {
-  int64_t n_rows = 0, nnz = 0;
-  const int32_t* row_ptr = nullptr;
-  const int32_t* col = nullptr;     // padded like CsrDev::col
-  const double* val = nullptr;
-  const float* val32 = nullptr;
-  int prefetch = 0;
-  bool val32_special = false;
-};
-
-// Halo part of a split: rows listed in `rows`, CRS over them.
-struct HaloDev {
-  int64_t n_rows = 0, nnz = 0;
-  const int32_t* rows = nullptr;
-  const int32_t* row_ptr = nullptr;
-  const int32_t* col = nullptr;
-  const double* val = nullptr;
-  const float* val32 = nullptr;
-  bool val32_special = false;
-};
 
 // ------------------------------------------------------- plan accessors
 const CsrDev* plan_csr(spmv_handle h);              // device view of the whole matrix
@@ -132,6 +69,13 @@ void build_sell(const HostCsr& A, int64_t C, int64_t sigma, SellHost* out);
 void build_split(const HostCsr& A, int64_t h, SplitHost* out);
 // False (reason in *why) unless A is square and symmetric in the sense of spmv_set_variant.
 bool build_sym(const HostCsr& A, SymHost* out, std::string* why);
+// Reverse Cuthill-McKee permutation (perm[new] = old) of a square pattern.
+bool rcm_permutation(int64_t n, const int32_t* row_ptr, const int32_t* col, int32_t* perm);
+// True if perm is a permutation of 0..n-1; fills inv (inv[old] = new).
+bool validate_permutation(int64_t n, const int32_t* perm, std::vector<int32_t>* inv, std::string* why);
+// A' = P A P^T: row r of A' is row perm[r] of A, columns relabelled by inv and sorted (stable).
+void permute_csr(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, const int32_t* perm,
+                 const std::vector<int32_t>& inv, int32_t* out_row_ptr, int32_t* out_col, double* out_val);
 void compute_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
                       int k, double* f);
 

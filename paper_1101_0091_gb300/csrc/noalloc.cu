@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "batch_kernel.cuh"
+#include "internal.h"
 
 namespace spmv {
 

@@ -19,6 +19,7 @@
 #include <new>
 
 #include "device.cuh"
+#include "internal.h"
 
 namespace spmv {
 

@@ -5,6 +5,7 @@
 #include <thread>
 
 #include "device.cuh"
+#include "internal.h"
 
 namespace spmv {
 
