@@ -12,7 +12,7 @@
 
 namespace spmv {
 
-template <typename VT, int K>
+template <typename VT, int K, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_sell(int64_t n_rows, int64_t n_chunks, const int32_t* __restrict__ perm,
            const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ chunk_len,
@@ -53,10 +53,21 @@ __global__ void __launch_bounds__(kThreads)
       b[u] = B + (int64_t)ldcs(col + slot) * ldb;
     }
     double g[NB][K];
+    if (VEC) {  // k == K >= 8, 16-byte aligned rows of B: one 16-byte gather per two columns
 #pragma unroll
-    for (int u = 0; u < NB; ++u)
+      for (int u = 0; u < NB; ++u)
 #pragma unroll
-      for (int q = 0; q < K; ++q) g[u][q] = (j + u < len && q < k) ? __ldg(b[u] + q) : 0.0;
+        for (int q = 0; q < K; q += 2) {
+          const double2 t2 = j + u < len ? __ldg(reinterpret_cast<const double2*>(b[u] + q)) : make_double2(0.0, 0.0);
+          g[u][q] = t2.x;
+          g[u][q + 1] = t2.y;
+        }
+    } else {
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) g[u][q] = (j + u < len && q < k) ? __ldg(b[u] + q) : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -65,6 +76,11 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (r >= n_rows) return;
   double* out = C + (int64_t)__ldg(perm + r) * ldc;
+  if (VEC) {
+#pragma unroll
+    for (int q = 0; q < K; q += 2) reinterpret_cast<double2*>(out)[q / 2] = make_double2(acc[q], acc[q + 1]);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < K; ++q)
     if (q < k) out[q] = acc[q];
@@ -76,8 +92,14 @@ static cudaError_t launch_sell_t(const SellDev& S, const VT* val, const double* 
   if (S.n_chunks == 0) return cudaSuccess;
   const int64_t threads = S.n_chunks * kSellC;
   const int64_t grid = (threads + kThreads - 1) / kThreads;
-  k_sell<VT, K><<<(unsigned)grid, kThreads, 0, s>>>(S.n_rows, S.n_chunks, S.perm, S.chunk_ptr, S.chunk_len, S.col,
-                                                    val, B, ldb, C, ldc, k, S.prefetch);
+  const bool vec = K >= 8 && k == K && ldb % 2 == 0 && ldc % 2 == 0 && (((uintptr_t)B | (uintptr_t)C) & 15) == 0;
+  if (vec)
+    k_sell<VT, K, (K >= 8)><<<(unsigned)grid, kThreads, 0, s>>>(S.n_rows, S.n_chunks, S.perm, S.chunk_ptr,
+                                                                 S.chunk_len, S.col, val, B, ldb, C, ldc, k,
+                                                                 S.prefetch);
+  else
+    k_sell<VT, K, false><<<(unsigned)grid, kThreads, 0, s>>>(S.n_rows, S.n_chunks, S.perm, S.chunk_ptr,
+                                                             S.chunk_len, S.col, val, B, ldb, C, ldc, k, S.prefetch);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,7 @@ __device__ __forceinline__ void prefetch_block(const uint32_t* __restrict__ blk,
   prefetch_l2(col + c_lo, (uint32_t)(c_hi - c_lo) * 4u);
 }
 
-template <typename VT, int K>
+template <typename VT, int K, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_crs_staged(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                  const VT* __restrict__ val, const uint32_t* __restrict__ blk, int64_t n_blk, int tile,
@@ -134,10 +134,21 @@ __global__ void __launch_bounds__(kThreads)
       b[u] = B + (int64_t)scol[jj - c_lo] * ldb;
     }
     double g[NB][K];
+    if (VEC) {  // k == K >= 8, 16-byte aligned rows of B: one 16-byte gather per two columns
 #pragma unroll
-    for (int u = 0; u < NB; ++u)
+      for (int u = 0; u < NB; ++u)
 #pragma unroll
-      for (int q = 0; q < K; ++q) g[u][q] = (j + u < re && q < k) ? __ldg(b[u] + q) : 0.0;
+        for (int q = 0; q < K; q += 2) {
+          const double2 t2 = j + u < re ? __ldg(reinterpret_cast<const double2*>(b[u] + q)) : make_double2(0.0, 0.0);
+          g[u][q] = t2.x;
+          g[u][q + 1] = t2.y;
+        }
+    } else {
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) g[u][q] = (j + u < re && q < k) ? __ldg(b[u] + q) : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -145,16 +156,21 @@ __global__ void __launch_bounds__(kThreads)
         if (j + u < re && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
   }
   double* out = C + (int64_t)row * ldc;
+  if (VEC) {
+#pragma unroll
+    for (int q = 0; q < K; q += 2) reinterpret_cast<double2*>(out)[q / 2] = make_double2(acc[q], acc[q + 1]);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < K; ++q)
     if (q < k) out[q] = accumulate ? out[q] + acc[q] : acc[q];
 }
 
-template <typename VT, int K>
-static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
+template <typename VT, int K, bool VEC>
+static cudaError_t launch_staged_v(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
                                    int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
   const size_t smem = sizeof(VT) * (size_t)(A.tile + 8) + 4 * (size_t)(A.tile + 8);
-  auto kern = k_crs_staged<VT, K>;
+  auto kern = k_crs_staged<VT, K, VEC>;
   static int smem_set[64] = {0};  // per device: largest dynamic shared memory size enabled so far
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -167,6 +183,15 @@ static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double*
   kern<<<(unsigned)A.n_blk, kThreads, smem, s>>>(A.row_ptr, A.col, val, A.blk, A.n_blk, A.tile, A.prefetch, B,
                                                   ldb, C, ldc, k, accumulate ? 1 : 0, status);
   return cudaGetLastError();
+}
+
+template <typename VT, int K>
+static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
+                                   int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
+  const bool vec = K >= 8 && k == K && !accumulate && ldb % 2 == 0 && ldc % 2 == 0 &&
+                   (((uintptr_t)B | (uintptr_t)C) & 15) == 0;
+  if (vec) return launch_staged_v<VT, K, (K >= 8)>(A, val, B, ldb, C, ldc, k, accumulate, status, s);
+  return launch_staged_v<VT, K, false>(A, val, B, ldb, C, ldc, k, accumulate, status, s);
 }
 
 template <typename VT>
