@@ -134,6 +134,16 @@ def ncu_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def dram_view(traffic, bytes_min, nnz, kern_s, hbm, pm) -> dict:
+    """From the recorded ncu DRAM bytes of the kernel: DRAM GB/s over the
+    measured launch time, its fraction of the copy peak, and kappa_gpu =
+    (DRAM bytes - V_min) / nnz."""
+    if traffic is None:
+        return {"dram_gbs": None, "dram_frac": None, "kappa_gpu": None}
+    return {"dram_gbs": round(traffic / kern_s / 1e9, 1), "dram_frac": round(traffic / kern_s / 1e9 / hbm, 4),
+            "kappa_gpu": round(pm.kappa_gpu(traffic, bytes_min, nnz), 4)}
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons; summary() keeps
     the samples taken inside [t0, t1] (host wall clock)."""
@@ -334,11 +344,13 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
                           if tr.bytes_min > 2 * 129e6 else "inputs L2-resident (warm figure)"),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "hbm_gbs": round(achieved, 1),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "peak_kind": hbm_kind,
-                     "traffic": ncu_traffic(kname, args.workload),
-                     "algorithmic_bytes_per_launch": tr.bytes_min,
-                     "fp64_frac": round(tr.flops / kern_s / 1e9 / FP64_PEAK_GFLOPS, 4)},
+        "roofline": dict({"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(achieved / hbm, 4), "peak_kind": hbm_kind,
+                          "traffic": ncu_traffic(kname, args.workload),
+                          "algorithmic_bytes_per_launch": tr.bytes_min,
+                          "frac_of_nominal_7900": round(achieved / 7900.0, 4),
+                          "fp64_frac": round(tr.flops / kern_s / 1e9 / FP64_PEAK_GFLOPS, 4)},
+                         **dram_view(ncu_traffic(kname, args.workload), tr.bytes_min, A.nnz, kern_s, hbm, pm)),
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
         "wall_s_timed": round(r["wall_s"], 4),
@@ -391,6 +403,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         import oracle
         ts = time_oracle(lambda: oracle.spmv(A, Bh) if k == 1 else oracle.spmm(A, Bh), 3, budget_s=30.0)
         line["cpu_baseline"] = {"value": round(tr.flops / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                                "host_cores": os.cpu_count(),
                                 "kind": "oracle", "sample": f"full product, best of {len(ts)} single-threaded runs"}
     plan.close()
     return line
@@ -410,6 +423,24 @@ def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
         t = med(lambda: plan.apply(B, C, stream))
         forms[name] = {"gflops": round(tr.flops / t / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t / 1e9, 1)}
     plan.set_variant(*VARIANTS["crs_l1"])
+    # cold figure: L2 flushed (a write of 2 x the L2 size) before every timed launch
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    cold = []
+    for i in range(25):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.apply(B, C, stream)
+        e1.record(stream)
+        stream.synchronize()
+        if i >= 5:
+            cold.append(e0.elapsed_time(e1) / 1e3)
+    t_cold = statistics.median(cold)
+    forms["crs_l1_cold"] = {"gflops": round(tr.flops / t_cold / 1e9, 1), "hbm_gbs": round(tr.bytes_min / t_cold / 1e9, 1),
+                            "flush_bytes": 2 * l2, "note": "L2 flushed before each launch; the row above is warm"}
+    del flush
     with spmv.Plan.from_csr(A, val_fp32=True) as p32:
         t = med(lambda: p32.apply(B, C, stream))
         tr32 = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4)
@@ -725,6 +756,7 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         ts = time_oracle(lambda: [oracle.spmm(A, B) for A, B in zip(As[:sub], Bhs[:sub])], 1, budget_s=30.0)
         fl = sum(8 * A.nnz for A in As[:sub])
         line["cpu_baseline"] = {"value": round(fl / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                                "host_cores": os.cpu_count(),
                                 "kind": "oracle", "sample": f"first {sub} members, k=4, best of {len(ts)}"}
     batch.close()
     for p in plans:
