@@ -373,6 +373,15 @@ spmv_status spmv_model_train_step(spmv_model_handle m, const float* X_dev, const
  * float32[M x n_out]) may be NULL.  Synchronises the stream. */
 spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32_t M, int32_t* choice,
                               float* predicted, void* stream);
+/* Pick a plan's kernel with the cost model: the plan's 34 features for k
+ * right-hand sides (spmv_features) go through the network (n_in must be 34),
+ * output o stands for variant variants[o] with SELL sigma sigmas[o] (host
+ * arrays of the network's n_out entries), and the plan switches to the
+ * output with the smallest prediction as spmv_set_variant would.  *choice
+ * (host) receives o.  Synchronises the stream. */
+spmv_status spmv_select(spmv_handle h, spmv_model_handle m, int32_t k, const int32_t* variants,
+                        const int32_t* sigmas, int32_t* choice, void* stream);
+
 /* Checkpoint with the normaliser, parameters and Adam state (binary file). */
 spmv_status spmv_model_save(spmv_model_handle m, const char* path);
 spmv_status spmv_model_load(spmv_model_handle* out, const char* path);

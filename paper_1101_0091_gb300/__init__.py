@@ -143,6 +143,17 @@ class Plan:
                                                                      "sell_val")))
         return out
 
+    def select(self, model_handle, k: int, outputs) -> int:
+        """spmv_select: run the cost model on this plan's features for k
+        right-hand sides and switch to its choice; outputs[o] = (variant, sigma)
+        for network output o.  Returns o."""
+        v = np.ascontiguousarray([o[0] for o in outputs], dtype=np.int32)
+        sg = np.ascontiguousarray([o[1] for o in outputs], dtype=np.int32)
+        ch = np.zeros(1, np.int32)
+        _b._check(_b.load().spmv_select(self.handle, model_handle, k, v.ctypes.data, sg.ctypes.data,
+                                        ch.ctypes.data, _stream_handle(None)))
+        return int(ch[0])
+
     def sym_export(self) -> dict:
         i = self.info()
         out = {"row_ptr": np.empty(i.n_rows + 1, np.int32), "col": np.empty(i.sym_nnz, np.int32),

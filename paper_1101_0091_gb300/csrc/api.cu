@@ -609,6 +609,28 @@ spmv_status spmv_sell_export(spmv_handle h, int32_t* perm, int64_t* chunk_ptr, i
   return SPMV_OK;
 }
 
+spmv_status spmv_select(spmv_handle h, spmv_model_handle m, int32_t k, const int32_t* variants,
+                        const int32_t* sigmas, int32_t* choice, void* stream) {
+  if (!h || !m || !variants || !sigmas || !choice) return fail(SPMV_ERR_ARG, "NULL argument");
+  if (k < 1 || k > h->opt.max_k) return fail(SPMV_ERR_ARG, "k out of range 1..max_k");
+  int32_t n_in = 0, n_hidden = 0, n_out = 0;
+  int64_t n_params = 0;
+  int32_t steps = 0;
+  spmv_status st = spmv_model_info(m, &n_in, &n_hidden, &n_out, &n_params, &steps);
+  if (st != SPMV_OK) return st;
+  if (n_in != 34) return fail(SPMV_ERR_ARG, "the model must take the 34 matrix features");
+  double f[34];
+  compute_features(h->host.n_rows, h->host.n_cols, h->host.row_ptr.data(), h->host.col.data(), k, f);
+  int32_t o = 0;
+  st = spmv_model_select(m, f, 1, &o, nullptr, stream);
+  if (st != SPMV_OK) return st;
+  DeviceGuard g(h->device);
+  st = prepare_variant(h, variants[o], sigmas[o]);
+  if (st != SPMV_OK) return st;
+  *choice = o;
+  return SPMV_OK;
+}
+
 spmv_status spmv_sym_export(spmv_handle h, int32_t* row_ptr, int32_t* col, double* val) {
   if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
   if (!h->sym.row_ptr) return fail(SPMV_ERR_UNSUPPORTED, "no SYM triangle built (set_variant SYM first)");

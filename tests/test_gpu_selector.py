@@ -47,3 +47,36 @@ def test_selector_gains_over_default_on_held_out(trained):
     assert t_learned < 0.8 * t_default           # the network's gain over CRS_L1 everywhere
     assert learned["total"] < default["total"]
     assert learned["total"] < 0.5
+
+
+def test_plan_select_switches_to_the_model_choice(lib):
+    """spmv_select: a network whose weights are zero predicts its output biases
+    for every matrix, so the plan switches to the output with the smallest
+    bias; the product then follows the oracle."""
+    from gpu_util import assert_close, run
+    F, H = 34, 8
+    outputs = [(lib.SPMV_CRS_L1, 1), (lib.SPMV_SELL, 256), (lib.SPMV_CRS_STAGED, 1), (lib.SPMV_SYM, 1)]
+    V = len(outputs)
+    A = gen.poisson3d_var(16)
+    B = gen.uniform(A.n_cols, seed=4)
+    for best in range(V):
+        params = np.zeros(H * F + H + H * H + H + V * H + V, np.float32)
+        bias = np.full(V, 3.0, np.float32)
+        bias[best] = -1.0
+        params[-V:] = bias
+        m = lib.spmv_model_create(F, H, V, params)
+        try:
+            with lib.Plan.from_csr(A) as p:
+                o = p.select(m, 1, outputs)
+                assert o == best
+                assert p.info().variant == outputs[best][0]
+                assert_close(run(p, B), A, B)
+        finally:
+            lib.spmv_model_destroy(m)
+    with lib.Plan.from_csr(A) as p:
+        m = lib.spmv_model_create(3, H, V, np.zeros(H * 3 + H + H * H + H + V * H + V, np.float32))
+        try:
+            with pytest.raises(lib.SpmvError):
+                p.select(m, 1, outputs)
+        finally:
+            lib.spmv_model_destroy(m)
