@@ -209,23 +209,42 @@ __device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, co
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q] = 0.0;
     constexpr int NB = K <= 2 ? 4 / K : 1;  // gathers issued before their FMAs
-    for (int j = 0; j < len; j += NB) {
-      double v[NB];
-      const double* b[NB];
-#pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int64_t slot = base + (int64_t)((j + u < len) ? j + u : j) * 32;
-        v[u] = ldcs(S.val + slot);
-        b[u] = M.B + (int64_t)ldcs(S.col + slot) * M.ldb;
-      }
-      double g[NB][K];
-#pragma unroll
-      for (int u = 0; u < NB; ++u) gather_row<K, VEC>(b[u], k, g[u]);
-#pragma unroll
-      for (int u = 0; u < NB; ++u)
+    if (NB == 1) {
+      // one slot per step, software-pipelined: the next slot's val/col load is in flight
+      // while this slot's gathers are, so only the gathers stay on the critical path
+      double v = len > 0 ? ldcs(S.val + base) : 0.0;
+      int32_t cc = len > 0 ? ldcs(S.col + base) : 0;
+      for (int j = 0; j < len; ++j) {
+        double g[K];
+        gather_row<K, VEC>(M.B + (int64_t)cc * M.ldb, k, g);
+        const int64_t nxt = base + (int64_t)(j + 1 < len ? j + 1 : j) * 32;
+        const double v_n = ldcs(S.val + nxt);
+        const int32_t c_n = ldcs(S.col + nxt);
 #pragma unroll
         for (int q = 0; q < K; ++q)
-          if (j + u < len && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
+          if (q < k) acc[q] = fma(v, g[q], acc[q]);
+        v = v_n;
+        cc = c_n;
+      }
+    } else {
+      for (int j = 0; j < len; j += NB) {
+        double v[NB];
+        const double* b[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int64_t slot = base + (int64_t)((j + u < len) ? j + u : j) * 32;
+          v[u] = ldcs(S.val + slot);
+          b[u] = M.B + (int64_t)ldcs(S.col + slot) * M.ldb;
+        }
+        double g[NB][K];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) gather_row<K, VEC>(b[u], k, g[u]);
+#pragma unroll
+        for (int u = 0; u < NB; ++u)
+#pragma unroll
+          for (int q = 0; q < K; ++q)
+            if (j + u < len && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
+      }
     }
     if (r >= 0) {
       double* out = Mp->C + (int64_t)r * Mp->ldc;
