@@ -49,6 +49,15 @@ VARIANTS = {"crs_staged": (1, 1), "crs_l1": (2, 1), "crs_l2": (3, 1), "crs_l4": 
             "sym": (9, 1)}
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# The paper's own single-socket CRS numbers (Sec. 2), quoted as context only: other hardware,
+# other (real) matrix; its multi-node results (QDR-InfiniBand Westmere cluster, Cray XE6) exist
+# only as figures.
+PAPER_CONTEXT = {"hardware": "Intel Xeon X5550 (Nehalem EP), one socket, 4 cores, 3 x DDR3-1333",
+                 "matrix": "HMeP Hamiltonian, N = 6.2e6, Nnzr ~ 15, FP64 CRS",
+                 "spmvm_gflops": 2.25, "spmvm_gbs": 18.1, "model_limit_gflops_at_spmvm_bw": 2.66,
+                 "kappa_bytes_per_nnz": 2.5, "hmep_kappa": 3.79,
+                 "multi_node": "QDR-InfiniBand Westmere cluster and Cray XE6: figures only, no numbers",
+                 "note": "context, not a target: no vs_baseline is computed from it"}
 
 
 def parse():
@@ -354,6 +363,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
         "wall_s_timed": round(r["wall_s"], 4),
+        "paper_context": PAPER_CONTEXT,
     }
     if not args.no_e2e:
         # through the C ABI from pinned host buffers: every step copies its B in (H2D) and its C out (D2H)
