@@ -415,6 +415,15 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         line["cpu_baseline"] = {"value": round(tr.flops / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
                                 "host_cores": os.cpu_count(),
                                 "kind": "oracle", "sample": f"full product, best of {len(ts)} single-threaded runs"}
+        import baselines
+        if baselines.available() and k == 1:
+            baselines.spmv(A, Bh)  # warm-up (first touch, thread start)
+            tn = time_oracle(lambda: baselines.spmv(A, Bh), 5, budget_s=15.0)
+            line["cpu_node_baseline"] = {
+                "value": round(tr.flops / min(tn) / 1e9, 4), "unit": "GFlop/s", "cores": baselines.threads(),
+                "kind": "OpenMP row-parallel CRS loop (the paper's node-level scheme), same arithmetic as the oracle",
+                "sample": f"full product, best of {len(tn)}",
+                "gpu_over_cpu_node": round(line["value"] / world / (tr.flops / min(tn) / 1e9), 1)}
     plan.close()
     return line
 
