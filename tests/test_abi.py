@@ -59,7 +59,8 @@ def bad_create(n_rows, n_cols, rp, ci, va):
     return e.value
 
 
-@pytest.mark.parametrize("case", ["row_ptr0", "decreasing", "col_high", "col_negative", "neg_dim"])
+@pytest.mark.parametrize("case", ["row_ptr0", "decreasing", "col_high", "col_negative", "neg_dim",
+                                  "rows_over_int32", "cols_over_int32"])
 def test_malformed_csr_rejected_on_host(built, case):
     """CRS validation runs on the host before any device call (no GPU needed)."""
     rp, ci, va, n, m = [0, 2, 3], [0, 1, 2], [1.0, 2.0, 3.0], 2, 3
@@ -73,6 +74,10 @@ def test_malformed_csr_rejected_on_host(built, case):
         ci = [0, -1, 2]
     elif case == "neg_dim":
         n = -1
+    elif case == "rows_over_int32":      # the size limits of the int32 index arrays
+        n = 2**31                        # (checked before any array is read)
+    elif case == "cols_over_int32":
+        m = 2**31 + 5
     err = bad_create(n, m, rp, ci, va)
     assert err.status == 2  # SPMV_ERR_CSR
 
