@@ -53,7 +53,8 @@ typedef enum {
 } spmv_status;
 
 /* Kernel variants.  All compute the same product with FP64 accumulation and
- * one fused multiply-add per stored entry. */
+ * one fused multiply-add per stored entry (SYM: per stored off-diagonal entry
+ * also one multiply for its mirror product). */
 typedef enum {
   SPMV_VARIANT_AUTO = 0,   /* the plan's default: CRS_L1 (a tuner or the cost model may switch)  */
   SPMV_CRS_STAGED = 1,     /* thread per row; each CTA's contiguous val/col tile is brought     */
