@@ -12,6 +12,8 @@
 // reductions at all for these rows.  A "warp" block holds up to 8 rows longer
 // than 64 entries, one warp per row: lanes stride the row with coalesced loads
 // and a 5-step xor-shuffle tree sums their partials.
+#include <mutex>
+
 #include "device.cuh"
 
 namespace spmv {
@@ -171,14 +173,20 @@ static cudaError_t launch_staged_v(const CsrDev& A, const VT* val, const double*
                                    int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
   const size_t smem = sizeof(VT) * (size_t)(A.tile + 8) + 4 * (size_t)(A.tile + 8);
   auto kern = k_crs_staged<VT, K, VEC>;
-  static int smem_set[64] = {0};  // per device: largest dynamic shared memory size enabled so far
+  // per device: largest dynamic shared memory size enabled so far (check and set under a lock, so
+  // that concurrent host threads never leave the attribute below the recorded size)
+  static int smem_set[64] = {0};
+  static std::mutex smem_mu;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 64 || (int)smem > smem_set[dev]) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev < 64) smem_set[dev] = (int)smem;
+  {
+    std::lock_guard<std::mutex> lock(smem_mu);
+    if (dev >= 64 || (int)smem > smem_set[dev]) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev < 64) smem_set[dev] = (int)smem;
+    }
   }
   kern<<<(unsigned)A.n_blk, kThreads, smem, s>>>(A.row_ptr, A.col, val, A.blk, A.n_blk, A.tile, A.prefetch, B,
                                                   ldb, C, ldc, k, accumulate ? 1 : 0, status);
