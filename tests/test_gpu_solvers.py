@@ -195,3 +195,14 @@ def test_cg_full_size_poisson280(lib):
         nb = np.linalg.norm(B[:, c])
         assert abs(math.sqrt(rr[c]) - np.linalg.norm(R_true[:, c])) <= 1e-9 * nb
         assert math.sqrt(rr[c]) < 0.5 * nb
+
+
+def test_solvers_on_an_empty_matrix(lib):
+    import torch
+    A = gen.CSR(0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    with lib.Plan.from_csr(A) as p, lib.Solver(p, 2) as s:
+        Bd = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+        it, rr, summ = s.cg(Bd, Bd.clone(), max_iter=10, rtol=1e-8)
+        assert np.all(it == 0) and summ.converged == 2
+        a, b = s.lanczos(Bd, 3)
+        assert np.all(a == 0) and np.all(b == 0)
