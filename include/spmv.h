@@ -423,7 +423,8 @@ spmv_status spmv_solver_destroy(spmv_solver_handle s);
  * (exactly as it is) once |R| <= rtol |B|, or on breakdown (P.Q <= 0); the
  * call returns when every column has stopped or after max_iter iterations.
  * The host polls the device every check_every iterations (those iterations
- * run from a CUDA graph captured on first use for these B, X and check_every).
+ * run from a CUDA graph captured on first use for these B, X and check_every,
+ * and captured again after the plan's variant or tuning changes).
  * iterations_host[k] and rr_host[k] (final R.R) may be NULL.  Synchronous. */
 spmv_status spmv_cg_solve(spmv_solver_handle s, const double* B_dev, double* X_dev, int32_t max_iter,
                           double rtol, int32_t check_every, void* stream, int32_t* iterations_host,

@@ -86,6 +86,7 @@ using namespace spmv;
 
 struct spmv_plan {
   int device = 0;
+  uint64_t generation = 0;  // bumped whenever the kernel, its arrays or its launch parameters change
   spmv_options opt{};
   int variant = SPMV_CRS_STAGED;
   HostCsr host;
@@ -147,6 +148,7 @@ const int32_t* plan_host_col(spmv_handle h) { return h->host.col.data(); }
 const double* plan_host_val(spmv_handle h) { return h->host.val.data(); }
 int plan_device(spmv_handle h) { return h->device; }
 int plan_max_k(spmv_handle h) { return h->opt.max_k; }
+uint64_t plan_generation(spmv_handle h) { return h->generation; }
 }  // namespace spmv
 
 static spmv_status build_blocks(spmv_plan* p, CsrDev* M, const int32_t* host_row_ptr) {
@@ -301,6 +303,7 @@ static spmv_status prepare_variant(spmv_plan* p, int variant, int sigma) {
     if (st != SPMV_OK) return st;
   }
   p->variant = variant;
+  ++p->generation;
   return SPMV_OK;
 }
 
@@ -550,6 +553,7 @@ spmv_status spmv_set_tuning(spmv_handle h, const spmv_tuning* t) {
   if (t->prefetch_distance < 0) return fail(SPMV_ERR_ARG, "prefetch_distance must be >= 0");
   h->tuning = *t;
   apply_tuning(h);
+  ++h->generation;
   return SPMV_OK;
 }
 

@@ -59,6 +59,9 @@ const int32_t* plan_host_col(spmv_handle h);        // host copy of col_idx
 const double* plan_host_val(spmv_handle h);         // host copy of val
 int plan_device(spmv_handle h);
 int plan_max_k(spmv_handle h);                     // largest k accepted by spmv_apply_block
+// Changes whenever the plan's kernel, its device arrays or its launch parameters change (work
+// captured into a CUDA graph through the plan must be captured again).
+uint64_t plan_generation(spmv_handle h);
 
 // ------------------------------------------------------- host builders
 bool validate_csr(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,

@@ -552,6 +552,7 @@ struct spmv_solver {
   const double* g_B = nullptr;
   double* g_X = nullptr;
   int g_steps = 0;
+  uint64_t g_gen = 0;              // plan generation the graph was captured at
 };
 
 static void solver_free(spmv_solver* s) {
@@ -671,7 +672,9 @@ spmv_status spmv_cg_solve(spmv_solver_handle S, const double* B_dev, double* X_d
                                   S->buf[1], S->partial, S->counter, S->cg, rtol * rtol);
     if (e != cudaSuccess) return cuda_fail(e, "CG init launch");
     const int steps = check_every < max_iter ? check_every : (max_iter > 0 ? max_iter : 1);
-    if (max_iter > 0 && (!S->graph || S->g_B != B_dev || S->g_X != X_dev || S->g_steps != steps)) {
+    const uint64_t gen = plan_generation(S->A);
+    if (max_iter > 0 &&
+        (!S->graph || S->g_B != B_dev || S->g_X != X_dev || S->g_steps != steps || S->g_gen != gen)) {
       if (S->graph) cudaGraphExecDestroy(S->graph);
       S->graph = nullptr;
       cudaGraph_t gr = nullptr;
@@ -693,6 +696,7 @@ spmv_status spmv_cg_solve(spmv_solver_handle S, const double* B_dev, double* X_d
       S->g_B = B_dev;
       S->g_X = X_dev;
       S->g_steps = steps;
+      S->g_gen = gen;
     }
     int done = 0;
     while (done < max_iter) {

@@ -206,3 +206,26 @@ def test_solvers_on_an_empty_matrix(lib):
         assert np.all(it == 0) and summ.converged == 2
         a, b = s.lanczos(Bd, 3)
         assert np.all(a == 0) and np.all(b == 0)
+
+
+def test_cg_recaptures_after_the_plan_changes(lib):
+    """The iterations replay from a captured graph; switching the plan's kernel
+    (here SELL with a new sigma, which rebuilds its arrays) or its tuning makes
+    the next solve capture again, so the results follow the oracle."""
+    import torch
+    A = gen.poisson3d_var(12)
+    B = gen.rhs_block(A.n_cols, 2, seed=12)
+    Xo, _ = osol.cg(A, B, max_iter=20, rtol=0.0)
+    with lib.Plan.from_csr(A, variant=lib.SPMV_SELL, sell_sigma=256) as p, lib.Solver(p, 2) as s:
+        Bd = dev(B)
+        Xd = torch.zeros_like(Bd)
+        for step in range(4):
+            if step == 1:
+                p.set_variant(lib.SPMV_SELL, 4096)
+            elif step == 2:
+                p.set_tuning(prefetch_distance=0)
+            elif step == 3:
+                p.set_variant(lib.SPMV_CRS_STAGED)
+            Xd.zero_()
+            s.cg(Bd, Xd, max_iter=20, rtol=0.0, check_every=20)
+            assert rel(host(Xd), Xo) < 1e-10, step
