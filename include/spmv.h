@@ -262,7 +262,8 @@ spmv_batch_config spmv_batch_default_config(void);
 
 /* Build a batch over `count` plans (same device) with k right-hand sides each
  * (1 <= k <= 16).  policies[count] (NULL: all SORTED) picks each member's row
- * policy.  Uploads the work list and the member table; no product runs. */
+ * policy.  Uploads the work list and the member table; no product runs.  The
+ * batch reads the plans' CRS arrays in place: the plans must outlive it. */
 spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_handle* plans, int32_t k,
                               const int32_t* policies, const spmv_batch_config* cfg);
 
