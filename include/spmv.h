@@ -384,6 +384,18 @@ spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32
 spmv_status spmv_select(spmv_handle h, spmv_model_handle m, int32_t k, const int32_t* variants,
                         const int32_t* sigmas, int32_t* choice, void* stream);
 
+/* Exhaustive timed sweep, the fallback of the cost model and the judge of its
+ * regret: for each candidate (variants[i], sigmas[i]), i < n, the product of
+ * k right-hand sides B_dev -> C_dev (layout as spmv_apply_block) is run once
+ * untimed and then `reps` times between CUDA events on `stream`; the plan
+ * switches to the candidate with the smallest median time.  *best (host)
+ * receives its index; times_ms[n] (host, may be NULL) the medians, +inf for
+ * a candidate the plan cannot build (e.g. SYM on an unsymmetric matrix).
+ * Returns SPMV_ERR_UNSUPPORTED if no candidate builds.  Synchronous. */
+spmv_status spmv_autotune(spmv_handle h, int32_t k, const double* B_dev, int64_t ldb, double* C_dev, int64_t ldc,
+                          const int32_t* variants, const int32_t* sigmas, int32_t n, int32_t reps, int32_t* best,
+                          float* times_ms, void* stream);
+
 /* Checkpoint with the normaliser, parameters and Adam state (binary file). */
 spmv_status spmv_model_save(spmv_model_handle m, const char* path);
 spmv_status spmv_model_load(spmv_model_handle* out, const char* path);

@@ -154,6 +154,21 @@ class Plan:
                                         ch.ctypes.data, _stream_handle(None)))
         return int(ch[0])
 
+    def autotune(self, B, C, candidates, k: int | None = None, reps: int = 7, stream=None):
+        """spmv_autotune: exhaustive timed sweep over candidates [(variant, sigma)];
+        the plan switches to the fastest.  Returns (index, median ms per candidate)."""
+        kk = 1 if B.dim() == 1 else (B.shape[1] if k is None else k)
+        ldb = 1 if B.dim() == 1 else B.stride(0)
+        ldc = 1 if C.dim() == 1 else C.stride(0)
+        v = np.ascontiguousarray([c[0] for c in candidates], dtype=np.int32)
+        sg = np.ascontiguousarray([c[1] for c in candidates], dtype=np.int32)
+        best = np.zeros(1, np.int32)
+        times = np.zeros(len(candidates), np.float32)
+        _b._check(_b.load().spmv_autotune(self.handle, kk, _ptr(B), ldb, _ptr(C), ldc, v.ctypes.data, sg.ctypes.data,
+                                          len(candidates), reps, best.ctypes.data, times.ctypes.data,
+                                          _stream_handle(stream)))
+        return int(best[0]), times
+
     def sym_export(self) -> dict:
         i = self.info()
         out = {"row_ptr": np.empty(i.n_rows + 1, np.int32), "col": np.empty(i.sym_nnz, np.int32),

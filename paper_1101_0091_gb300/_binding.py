@@ -66,6 +66,7 @@ _SIGS = {
     "spmv_split_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_sym_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_select": ([_vp, _vp, _i32, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_autotune": ([_vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp], ctypes.c_int),
     "spmv_features": ([_i64, _i64, _vp, _vp, _i32, _vp], ctypes.c_int),
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the library: plan lifecycle, the apply calls, variant switching and
 // the export of built index structures.  See include/spmv.h for the contract.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -632,6 +633,58 @@ spmv_status spmv_select(spmv_handle h, spmv_model_handle m, int32_t k, const int
   st = prepare_variant(h, variants[o], sigmas[o]);
   if (st != SPMV_OK) return st;
   *choice = o;
+  return SPMV_OK;
+}
+
+spmv_status spmv_autotune(spmv_handle h, int32_t k, const double* B_dev, int64_t ldb, double* C_dev, int64_t ldc,
+                          const int32_t* variants, const int32_t* sigmas, int32_t n, int32_t reps, int32_t* best,
+                          float* times_ms, void* stream) {
+  if (!h || !variants || !sigmas || !best || n < 1 || reps < 1) return fail(SPMV_ERR_ARG, "bad argument");
+  if (k < 1 || k > h->opt.max_k || ldb < k || ldc < k) return fail(SPMV_ERR_ARG, "bad k, ldb or ldc");
+  if (h->host.n_rows > 0 && (!C_dev || (!B_dev && h->host.n_cols > 0))) return fail(SPMV_ERR_ARG, "NULL buffer");
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int keep_variant = h->variant, keep_sigma = h->sell.perm ? h->sell.sigma : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SPMV_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  std::vector<float> med((size_t)n, INFINITY), t((size_t)reps);
+  int arg = -1;
+  spmv_status st = SPMV_OK;
+  for (int i = 0; i < n && st == SPMV_OK; ++i) {
+    if (prepare_variant(h, variants[i], sigmas[i]) != SPMV_OK) continue;  // not buildable for this matrix
+    cudaError_t e = run_variant(h, h->A, h->variant, B_dev, ldb, C_dev, ldc, k, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = run_variant(h, h->A, h->variant, B_dev, ldb, C_dev, ldc, k, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t[(size_t)r], e0, e1);
+    }
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "autotune launch");
+      break;
+    }
+    std::vector<float> sorted(t);
+    std::sort(sorted.begin(), sorted.end());
+    med[(size_t)i] = sorted[sorted.size() / 2];
+    if (arg < 0 || med[(size_t)i] < med[(size_t)arg]) arg = i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SPMV_OK) return st;
+  if (times_ms) std::memcpy(times_ms, med.data(), sizeof(float) * (size_t)n);
+  if (arg < 0) {
+    prepare_variant(h, keep_variant, keep_sigma);
+    return fail(SPMV_ERR_UNSUPPORTED, "no candidate variant could be built for this matrix");
+  }
+  st = prepare_variant(h, variants[arg], sigmas[arg]);
+  if (st != SPMV_OK) return st;
+  *best = arg;
   return SPMV_OK;
 }
 

@@ -80,3 +80,26 @@ def test_plan_select_switches_to_the_model_choice(lib):
                 p.select(m, 1, outputs)
         finally:
             lib.spmv_model_destroy(m)
+
+
+def test_native_exhaustive_sweep(lib):
+    """spmv_autotune times every candidate, switches the plan to the fastest
+    and skips candidates the matrix cannot build (SYM on an unsymmetric one)."""
+    import torch
+    from gpu_util import assert_close, host, run
+    A = gen.powerlaw(30_000, seed=8)
+    B = gen.uniform(A.n_cols, seed=8)
+    cands = [(lib.SPMV_CRS_L1, 1), (lib.SPMV_CRS_L4, 1), (lib.SPMV_CRS_L32, 1), (lib.SPMV_SELL, 256),
+             (lib.SPMV_CRS_STAGED, 1), (lib.SPMV_SYM, 1)]
+    with lib.Plan.from_csr(A) as p:
+        Bd = torch.from_numpy(B).cuda()
+        C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        best, times = p.autotune(Bd, C, cands, reps=5)
+        assert np.isinf(times[-1]) and np.all(np.isfinite(times[:-1]))
+        assert best == int(np.argmin(times))
+        assert p.info().variant == cands[best][0]
+        assert_close(run(p, B), A, B)
+        with pytest.raises(lib.SpmvError) as e:
+            p.autotune(Bd, C, [(lib.SPMV_SYM, 1)], reps=2)
+        assert e.value.status == 6
+        assert p.info().variant == cands[best][0]
