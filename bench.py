@@ -690,6 +690,19 @@ def block_precision_forms(A, torch, spmv, pm, stream):
     return out
 
 
+def mixed_row_bound(As, kern_s, hbm) -> dict:
+    """Per-row roofline of an uneven batch (k = 4): a row of L entries needs
+    12 L + 68 bytes (val/col, row pointer, its 32-byte C row and a 32-byte B row)
+    and 8 L flops, so short rows are HBM-bound and long ones FP64-bound; the
+    bound is the sum over rows of the larger of the two times."""
+    t = 0.0
+    for A in As:
+        L = np.diff(A.row_ptr).astype(np.float64)
+        t += float(np.maximum((12 * L + 68) / (hbm * 1e9), 8 * L / (FP64_PEAK_GFLOPS * 1e9)).sum())
+    return {"mixed_bound_us": round(t * 1e6, 1), "mixed_frac": round(t / kern_s, 4),
+            "mixed_bound_kind": "sum over rows of max(HBM time of 12L+68 B, FP64 time of 8L flops)"}
+
+
 def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     As, Bhs = batch_members(args.batch_count)
     nnz = sum(A.nnz for A in As)
@@ -726,7 +739,8 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
                      "unit": "GFLOP/s", "frac": round(achieved_gf / FP64_PEAK_GFLOPS, 4),
                      "peak_kind": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "traffic": ncu_traffic("batch", args.workload), "algorithmic_bytes_per_launch": bytes_min,
-                     "hbm_frac": round(bytes_min / kern_s / 1e9 / hbm, 4), "hbm_peak": hbm, "hbm_peak_kind": hbm_kind},
+                     "hbm_frac": round(bytes_min / kern_s / 1e9 / hbm, 4), "hbm_peak": hbm, "hbm_peak_kind": hbm_kind,
+                     **mixed_row_bound(As, kern_s, hbm)},
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
         "wall_s_timed": round(r["wall_s"], 4),
