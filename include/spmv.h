@@ -244,7 +244,7 @@ typedef enum {
   SPMV_BATCH_L32 = 4,     /* a warp per row                                          */
   SPMV_BATCH_ADAPT = 5,   /* rows binned by exact length (<= 32: one lane per row),   */
                           /* longer rows with about 32 entries per lane (L <= 32)     */
-  SPMV_BATCH_SORTED = 6,  /* rows of <= 32 entries copied into a length-sorted       */
+  SPMV_BATCH_SORTED = 6,  /* rows of <= 64 entries copied into a length-sorted       */
                           /* SELL-32 layout (coalesced, one lane per row); longer     */
                           /* rows as in ADAPT.  Costs a copy of those rows' entries.  */
   SPMV_BATCH_N_POLICIES = 7

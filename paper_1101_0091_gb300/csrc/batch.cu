@@ -10,7 +10,9 @@
 // ranges.  The adaptive policy bins rows by exact length (a counting sort), so
 // that the 32 rows of a warp pass have equal length and no lane idles on the
 // FP64 pipe; rows up to 32 entries get one lane, longer rows about 32 entries
-// per lane; inside a member, longer rows come first.  Items keep member order,
+// per lane; inside a member, longer rows come first.  The sorted policy (the
+// default) puts the rows of up to kSortedMaxLen entries into a length-sorted
+// SELL-32 copy and the longer ones into adaptive items.  Items keep member order,
 // which keeps the B blocks being gathered resident in L2.  No CTA ever waits
 // for another.
 #include <algorithm>
@@ -59,7 +61,14 @@ static void cut_items(const int32_t* rp, int64_t p0, int64_t p1, int mat, int L,
   if (p1 > s) out.push_back(BatchItem{mat, (int32_t)s, (int32_t)p1, (int32_t)len, (int16_t)L, (int16_t)mode, 0, 0});
 }
 
-// Length-sorted SELL-32 copy of the rows with at most 32 entries (sorted
+// Rows of at most this many entries go to the length-sorted SELL-32 copy
+// (sorted policy, one lane per row, coalesced slots); longer rows to
+// multi-lane CRS items.  Of 32 / 64 / 96 / 128, 64 gave the fastest
+// power-law batch (rows of 33-64 entries ran at 0.69 of the FP64 peak as
+// two-lane CRS items and at 0.96 in the sorted copy).
+constexpr int kSortedMaxLen = 64;
+
+// Length-sorted SELL-32 copy of the rows with at most kSortedMaxLen entries (sorted
 // policy), appended for one member: rows by descending length (stable), 32 per
 // chunk, chunk length = its first (longest) row, column-major slots, padding
 // val +0.0 with the row's last column (0 for empty and padding rows).
@@ -71,17 +80,17 @@ struct SortedSell {
 
 static void append_sorted_sell(const int32_t* rp, const int32_t* col, const double* val, int64_t n_rows,
                                SortedSell& S, int64_t* first_chunk, int64_t* n_chunks) {
-  int64_t cnt[34] = {0};
+  int64_t cnt[kSortedMaxLen + 2] = {0};
   for (int64_t r = 0; r < n_rows; ++r) {
     const int64_t len = rp[r + 1] - rp[r];
-    if (len <= 32) cnt[32 - len + 1]++;
+    if (len <= kSortedMaxLen) cnt[kSortedMaxLen - len + 1]++;
   }
-  for (int i = 1; i < 34; ++i) cnt[i] += cnt[i - 1];
-  const int64_t n_short = cnt[33];
+  for (int i = 1; i < kSortedMaxLen + 2; ++i) cnt[i] += cnt[i - 1];
+  const int64_t n_short = cnt[kSortedMaxLen + 1];
   std::vector<int32_t> order((size_t)n_short);
   for (int64_t r = 0; r < n_rows; ++r) {
     const int64_t len = rp[r + 1] - rp[r];
-    if (len <= 32) order[(size_t)cnt[32 - len]++] = (int32_t)r;
+    if (len <= kSortedMaxLen) order[(size_t)cnt[kSortedMaxLen - len]++] = (int32_t)r;
   }
   *first_chunk = (int64_t)S.chunk_len.size();
   *n_chunks = (n_short + 31) / 32;
@@ -165,7 +174,7 @@ void build_batch_items(const int32_t* rp, int64_t n_rows, int mat, int policy, i
     if (len > 32)
       while (e <= maxlen && adaptive_lanes(maxlen - e) == L && maxlen - e > 32) ++e;
     const int64_t p0 = start[(size_t)d], p1 = start[(size_t)e];
-    if (p1 > p0 && !(long_only && len <= 32))
+    if (p1 > p0 && !(long_only && len <= kSortedMaxLen))
       cut_items(rp, base + p0, base + p1, mat, L, len > 32 ? 2 : 1, len, item_nnz, out);
     d = e;
   }
