@@ -397,8 +397,10 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         line["forms"] = poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C)
     if "sym" in groups and k == 1 and (poisson or eigen):
         line.setdefault("forms", {}).update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
-    if "spmm" in groups and k == 1 and poisson:
-        line["spmm"] = spmm_forms(A, torch, spmv, pm, timer, stream)
+    if "spmm" in groups and k == 1 and (poisson or eigen):
+        line["spmm"] = spmm_forms(A, torch, spmv, pm, timer, stream,
+                                  ("crs_l1", "crs_staged", "sell_s256") if poisson else
+                                  ("crs_l1", "sell_s256", "sell_s4096"))
     if "solver" in groups and k == 1 and poisson:
         line["solver"] = cg_forms(A, torch, spmv, pm, stream)
     if "solver" in groups and k == 1 and eigen:
@@ -496,10 +498,11 @@ def sym_forms(A, torch, spmv, pm, timer, stream, B, C):
     return out
 
 
-def spmm_forms(A, torch, spmv, pm, timer, stream):
+def spmm_forms(A, torch, spmv, pm, timer, stream, names):
     """k right-hand sides on the full matrix (a11): median event time per
-    product for three kernels.  Each nonzero needs k FP64 FMAs, so for k >= 2
-    the bound is the FP64 pipe (2k nnz flops at 1258.6 GFLOP/s), not HBM."""
+    product for the named kernels.  Each nonzero needs k FP64 FMAs, so for
+    k >= 2 the bound is the FP64 pipe (2k nnz flops at 1258.6 GFLOP/s), not
+    HBM."""
     import gen
     hbm, _ = measured_hbm()
     out = {"bound": "max(V_min(k) / measured copy peak, 2 k nnz / FP64 peak)"}
@@ -511,7 +514,7 @@ def spmm_forms(A, torch, spmv, pm, timer, stream):
             tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
             t_bound = max(tr.bytes_min / (hbm * 1e9), tr.flops / (FP64_PEAK_GFLOPS * 1e9))
             row = {"bound_us": round(t_bound * 1e6, 1)}
-            for name in ("crs_l1", "crs_staged", "sell_s256"):
+            for name in names:
                 vid, sigma = VARIANTS[name]
                 p.set_variant(vid, sigma)
                 t = statistics.median(timer.run(lambda: p.apply_block(B, C, k, stream), 30, 3)["per_ms"]) / 1e3
@@ -587,11 +590,9 @@ def cg_forms(A, torch, spmv, pm, stream, iters: int = 50):
            "iterations": iters,
            "bound": "SpMM at max(HBM, FP64-pipe) time of its V_min and 2k nnz flops, plus the vector "
                     "kernels' 88 k n bytes at the measured copy peak (the kernels run one after another)"}
-    for k in (1, 4, 8):
-        # k = 1 is HBM-bound (CRS_L1); k >= 2 is FP64-pipe-bound: CRS_STAGED is the fastest kernel at k = 4,
-        # CRS_L1 with 16-byte gathers at k = 8
-        variant = spmv.SPMV_CRS_STAGED if k == 4 else spmv.SPMV_CRS_L1
-        with spmv.Plan.from_csr(A, variant=variant) as p:
+    for k in (1, 4, 8, 16):
+        # k = 1 is HBM-bound; k >= 2 is FP64-pipe-bound, where CRS_L1 runs its column-split form
+        with spmv.Plan.from_csr(A, variant=spmv.SPMV_CRS_L1) as p:
             B = torch.from_numpy(gen.rhs_block(A.n_cols, k, seed=0)).cuda()
             X = torch.zeros_like(B)
             stream.wait_stream(torch.cuda.current_stream())
@@ -610,7 +611,7 @@ def cg_forms(A, torch, spmv, pm, stream, iters: int = 50):
         spmm = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
         t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (FP64_PEAK_GFLOPS * 1e9))
                    + 88 * k * A.n_rows / (hbm * 1e9))
-        out[f"k{k}"] = {"plan_variant": "crs_staged" if k == 4 else "crs_l1",
+        out[f"k{k}"] = {"plan_variant": "crs_l1",
                         "us_per_iteration": round(t_it * 1e6, 1), "gflops": round(flops / t_it / 1e9, 1),
                         "hbm_gbs": round(byts / t_it / 1e9, 1), "bytes_per_iteration": byts,
                         "bound_us": round(t_bound * 1e6, 1), "frac_of_bound": round(t_bound / t_it, 4),

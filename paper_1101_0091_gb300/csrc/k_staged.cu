@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads)
       b[u] = B + (int64_t)scol[jj - c_lo] * ldb;
     }
     double g[NB][K];
-    if (VEC) {  // k == K >= 8, 16-byte aligned rows of B: one 16-byte gather per two columns
+    if (VEC) {  // k == K >= 2, 16-byte aligned rows of B: one 16-byte gather per two columns
 #pragma unroll
       for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -196,9 +196,9 @@ static cudaError_t launch_staged_v(const CsrDev& A, const VT* val, const double*
 template <typename VT, int K>
 static cudaError_t launch_staged_t(const CsrDev& A, const VT* val, const double* B, int64_t ldb, double* C,
                                    int64_t ldc, int k, bool accumulate, int* status, cudaStream_t s) {
-  const bool vec = K >= 8 && k == K && !accumulate && ldb % 2 == 0 && ldc % 2 == 0 &&
+  const bool vec = K >= 2 && k == K && !accumulate && ldb % 2 == 0 && ldc % 2 == 0 &&
                    (((uintptr_t)B | (uintptr_t)C) & 15) == 0;
-  if (vec) return launch_staged_v<VT, K, (K >= 8)>(A, val, B, ldb, C, ldc, k, accumulate, status, s);
+  if (vec) return launch_staged_v<VT, K, (K >= 2)>(A, val, B, ldb, C, ldc, k, accumulate, status, s);
   return launch_staged_v<VT, K, false>(A, val, B, ldb, C, ldc, k, accumulate, status, s);
 }
 

@@ -6,10 +6,10 @@
 //
 // Vectors are row-major n x k blocks (ld = k, 16-byte aligned: the vector
 // kernels move 16 bytes per access).  The vector work of an iteration is a few
-// fused grid-stride kernels on a fixed grid; each reduces
+// fused grid-stride kernels on a grid of one wave; each reduces
 // its per-column inner products to one partial per CTA, and the CTA that
-// finishes last (threadfence + ticket, no waiting) adds the partials in CTA
-// order and updates the per-column scalars in device memory.  Reductions are
+// finishes last (threadfence + ticket, no waiting) adds the partials in a
+// fixed order and updates the per-column scalars in device memory.  Reductions are
 // therefore deterministic for a given solver.  Columns freeze on the device the
 // iteration they converge (or break down), so the host only polls a counter
 // every `check_every` iterations; those iterations are replayed from a CUDA
@@ -37,95 +37,29 @@ struct LzScalars {
   int live[kMaxCols];
 };
 
-// Sum of x over the CTA for K columns; result valid in threads q < K of warp 0
-// (fixed shuffle tree, then warps in order).
-template <int K>
-__device__ __forceinline__ void block_sum(double (&x)[K], double (*sh)[K]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-    for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], off);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < K; ++q) sh[warp][q] = x[q];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += sh[w][q];
-      x[q] = s;
-    }
-  }
-}
-
-// Writes this CTA's NSUM x K partials, then returns true in the CTA that
-// finished last (all partials visible to it).
-template <int K, int NSUM>
-__device__ bool publish_partials(double (&x)[NSUM][K], double* partial, uint32_t* counter, int k) {
-  __shared__ double sh[kThreads / 32][K];
-  __shared__ bool last;
-#pragma unroll
-  for (int s = 0; s < NSUM; ++s) {
-    block_sum<K>(x[s], sh);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int q = 0; q < K; ++q)
-        if (q < k) partial[((size_t)blockIdx.x * NSUM + s) * kMaxCols + q] = x[s][q];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-// In the last CTA (all threads): the sums of the CTAs' partials, per sum s
-// and column q, into tot[s][q].  Thread t adds the partials of CTAs t, t+256,
-// ... in order, then the threads are combined by the fixed tree of block_sum.
-template <int K, int NSUM>
-__device__ void finish_partials(const double* partial, int k, double (&tot)[NSUM][K]) {
-  __shared__ double sh[kThreads / 32][K];
-  double x[NSUM][K];
-#pragma unroll
-  for (int s = 0; s < NSUM; ++s)
-#pragma unroll
-    for (int q = 0; q < K; ++q) x[s][q] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads)
-#pragma unroll
-    for (int s = 0; s < NSUM; ++s)
-#pragma unroll
-      for (int q = 0; q < K; ++q)
-        if (q < k) x[s][q] += __ldcg(partial + ((size_t)b * NSUM + s) * kMaxCols + q);
-#pragma unroll
-  for (int s = 0; s < NSUM; ++s) {
-    block_sum<K>(x[s], sh);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int q = 0; q < K; ++q) tot[s][q] = x[s][q];
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------- block walking
 // How a thread walks a row-major n x k block, one unit per grid-stride step:
 //  PAIRS (k = 1): two consecutive entries, one 16-byte access;
-//  VROWS (k = K even): one row of K values, K/2 16-byte accesses;
+//  VROWS (k = K = 2, 4): one row of K values, K/2 16-byte accesses;
+//  VGROUPS (k = K = 8, 16): a group of 4 columns of one row (K/4 units per
+//    row), two 16-byte accesses; a thread keeps 4 accumulators instead of K,
+//    which keeps these kernels at several CTAs per SM;
 //  ROWS (other k): one row, k scalar accesses (K >= k, masked).
-// PAIRS and VROWS need 16-byte aligned blocks (checked on the host).
-enum { ROWS = 0, VROWS = 1, PAIRS = 2 };
+// PAIRS, VROWS and VGROUPS need 16-byte aligned blocks (checked on the host).
+enum { ROWS = 0, VROWS = 1, PAIRS = 2, VGROUPS = 3 };
 
 template <int K, int MODE>
 struct Seg {
-  static constexpr int W = MODE == PAIRS ? 2 : K;   // values per unit
-  static constexpr int KC = MODE == PAIRS ? 1 : K;  // columns per unit
-  __device__ static int64_t units(int64_t n) { return MODE == PAIRS ? (n + 1) / 2 : n; }
-  __device__ static int col(int w) { return MODE == PAIRS ? 0 : w; }
-  __device__ static bool valid(int64_t u, int w, int64_t n, int k) {
-    return MODE == PAIRS ? 2 * u + w < n : w < k;
+  static constexpr int NG = MODE == VGROUPS ? K / 4 : 1;                    // units per row
+  static constexpr int W = MODE == PAIRS ? 2 : (MODE == VGROUPS ? 4 : K);  // values per unit
+  static constexpr int KC = MODE == PAIRS ? 1 : W;                         // accumulators per thread
+  static constexpr int KP = MODE == PAIRS ? 1 : K;                         // columns of the sums
+  static_assert(kThreads % NG == 0, "a thread's units must share one column group");
+  __device__ static int64_t units(int64_t n) { return MODE == PAIRS ? (n + 1) / 2 : n * NG; }
+  // accumulator of value w, and the block column it belongs to in unit u
+  __device__ static int acol(int w) { return MODE == PAIRS ? 0 : w; }
+  __device__ static int gcol(int64_t u, int w) {
+    return MODE == PAIRS ? 0 : (MODE == VGROUPS ? (int)(u % NG) * 4 + w : w);
   }
   __device__ static void load(const double* p, int64_t u, int64_t n, int k, double (&v)[W]) {
     if (MODE == PAIRS) {
@@ -137,10 +71,11 @@ struct Seg {
         v[0] = p[2 * u];
         v[1] = 0.0;
       }
-    } else if (MODE == VROWS) {
+    } else if (MODE == VROWS || MODE == VGROUPS) {
+      // VGROUPS: u * 4 is the offset of group u % NG of row u / NG
 #pragma unroll
       for (int h = 0; h < W / 2; ++h) {
-        const double2 t = reinterpret_cast<const double2*>(p + u * K)[h];
+        const double2 t = reinterpret_cast<const double2*>(p + u * W)[h];
         v[2 * h] = t.x;
         v[2 * h + 1] = t.y;
       }
@@ -155,9 +90,9 @@ struct Seg {
         reinterpret_cast<double2*>(p)[u] = make_double2(v[0], v[1]);
       else
         p[2 * u] = v[0];
-    } else if (MODE == VROWS) {
+    } else if (MODE == VROWS || MODE == VGROUPS) {
 #pragma unroll
-      for (int h = 0; h < W / 2; ++h) reinterpret_cast<double2*>(p + u * K)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+      for (int h = 0; h < W / 2; ++h) reinterpret_cast<double2*>(p + u * W)[h] = make_double2(v[2 * h], v[2 * h + 1]);
     } else {
 #pragma unroll
       for (int w = 0; w < W; ++w)
@@ -165,6 +100,78 @@ struct Seg {
     }
   }
 };
+
+// ---------------------------------------------------------------- reductions
+// Per-column sums over a CTA and then over the CTAs, in a fixed order (so a
+// solver's results do not depend on timing).
+
+// Writes this CTA's NS x KP column sums of the threads' accumulators
+// (G::KC per thread: thread t holds the columns of group t % G::NG, or all
+// of them), then returns true in the CTA that finished last (all partials
+// visible to it).  Order: xor-shuffle tree within each warp, then warps in
+// order.
+template <typename G, int NS>
+__device__ bool publish_partials(double (&acc)[NS][G::KC], double* partial, uint32_t* counter, int k) {
+  constexpr int KP = G::KP, KC = G::KC, R = G::NG;  // R lanes of a warp hold distinct column sets
+  __shared__ double sh[kThreads / 32][KP];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int w = 0; w < KC; ++w)
+#pragma unroll
+      for (int off = 16; off >= R; off >>= 1) acc[s][w] += __shfl_xor_sync(0xffffffffu, acc[s][w], off);
+    if (lane < R)
+#pragma unroll
+      for (int w = 0; w < KC; ++w) sh[warp][lane * KC + w] = acc[s][w];
+    __syncthreads();
+    if (threadIdx.x < KP && threadIdx.x < k) {
+      double t = 0.0;
+#pragma unroll
+      for (int v = 0; v < kThreads / 32; ++v) t += sh[v][threadIdx.x];
+      partial[((size_t)blockIdx.x * NS + s) * kMaxCols + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// In the last CTA (all threads): the sums of the CTAs' partials, per sum s
+// and column q, into tot[s][q].  Thread t takes column t % KP and adds the
+// partials of CTAs t / KP, t / KP + 256 / KP, ... in order; the threads of a
+// column are then combined by an xor-shuffle tree and the warps in order.
+template <int KP, int NS>
+__device__ void finish_partials(const double* partial, int k, double (&tot)[NS][KP]) {
+  constexpr int SL = kThreads / KP;  // threads per column
+  __shared__ double sh[kThreads / 32][KP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = threadIdx.x % KP;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = 0.0;
+    if (q < k)
+      for (unsigned b = threadIdx.x / KP; b < gridDim.x; b += SL)
+        x += __ldcg(partial + ((size_t)b * NS + s) * kMaxCols + q);
+#pragma unroll
+    for (int off = 16; off >= KP; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane < KP) sh[warp][lane] = x;
+    __syncthreads();
+    if (threadIdx.x < KP) {
+      double t = 0.0;
+#pragma unroll
+      for (int v = 0; v < kThreads / 32; ++v) t += sh[v][threadIdx.x];
+      tot[s][threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
 
 #define UNIT_LOOP(u, n) \
   for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < G::units(n); u += (int64_t)gridDim.x * kThreads)
@@ -187,15 +194,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(int64_t n, int k, const do
 #pragma unroll
     for (int w = 0; w < G::W; ++w) {
       r[w] = b[w] - r[w];
-      acc[0][G::col(w)] = fma(r[w], r[w], acc[0][G::col(w)]);
-      acc[1][G::col(w)] = fma(b[w], b[w], acc[1][G::col(w)]);
+      acc[0][G::acol(w)] = fma(r[w], r[w], acc[0][G::acol(w)]);
+      acc[1][G::acol(w)] = fma(b[w], b[w], acc[1][G::acol(w)]);
     }
     G::store(R, u, n, k, r);
     G::store(P, u, n, k, r);
   }
-  if (!publish_partials<G::KC, 2>(acc, partial, counter, k)) return;
-  __shared__ double tot[2][G::KC];
-  finish_partials<G::KC, 2>(partial, k, tot);
+  if (!publish_partials<G, 2>(acc, partial, counter, k)) return;
+  __shared__ double tot[2][G::KP];
+  finish_partials<G::KP, 2>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     const double rr = tot[0][q], bb = tot[1][q];
@@ -228,11 +235,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(int64_t n, int k, const d
     G::load(P, u, n, k, p);
     G::load(Q, u, n, k, q2);
 #pragma unroll
-    for (int w = 0; w < G::W; ++w) acc[0][G::col(w)] = fma(p[w], q2[w], acc[0][G::col(w)]);
+    for (int w = 0; w < G::W; ++w) acc[0][G::acol(w)] = fma(p[w], q2[w], acc[0][G::acol(w)]);
   }
-  if (!publish_partials<G::KC, 1>(acc, partial, counter, k)) return;
-  __shared__ double tot[1][G::KC];
-  finish_partials<G::KC, 1>(partial, k, tot);
+  if (!publish_partials<G, 1>(acc, partial, counter, k)) return;
+  __shared__ double tot[1][G::KP];
+  finish_partials<G::KP, 1>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     const double pq = tot[0][q];
@@ -253,9 +260,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, int k, double
                                                         const double* __restrict__ P, const double* __restrict__ Q,
                                                         double* partial, uint32_t* counter, CgScalars* S) {
   using G = Seg<K, MODE>;
-  __shared__ double s_alpha[G::KC];
-  __shared__ int s_active[G::KC];
-  if (threadIdx.x < G::KC) {
+  __shared__ double s_alpha[G::KP];
+  __shared__ int s_active[G::KP];
+  if (threadIdx.x < G::KP) {
     s_alpha[threadIdx.x] = threadIdx.x < k ? S->alpha[threadIdx.x] : 0.0;
     s_active[threadIdx.x] = threadIdx.x < k ? S->active[threadIdx.x] : 0;
   }
@@ -271,19 +278,19 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, int k, double
     G::load(Q, u, n, k, q2);
 #pragma unroll
     for (int w = 0; w < G::W; ++w) {
-      const int c = G::col(w);
+      const int c = G::gcol(u, w);
       if (s_active[c]) {
         x[w] = fma(s_alpha[c], p[w], x[w]);
         r[w] = fma(-s_alpha[c], q2[w], r[w]);
       }
-      acc[0][c] = fma(r[w], r[w], acc[0][c]);
+      acc[0][G::acol(w)] = fma(r[w], r[w], acc[0][G::acol(w)]);
     }
     G::store(X, u, n, k, x);
     G::store(R, u, n, k, r);
   }
-  if (!publish_partials<G::KC, 1>(acc, partial, counter, k)) return;
-  __shared__ double tot[1][G::KC];
-  finish_partials<G::KC, 1>(partial, k, tot);
+  if (!publish_partials<G, 1>(acc, partial, counter, k)) return;
+  __shared__ double tot[1][G::KP];
+  finish_partials<G::KP, 1>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     if (S->active[q]) {
@@ -306,10 +313,10 @@ template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads) k_cg_direction(int64_t n, int k, const double* __restrict__ R,
                                                            double* P, uint32_t* counter, CgScalars* S) {
   using G = Seg<K, MODE>;
-  __shared__ double s_beta[G::KC];
-  __shared__ int s_active[G::KC];
+  __shared__ double s_beta[G::KP];
+  __shared__ int s_active[G::KP];
   __shared__ bool last;
-  if (threadIdx.x < G::KC) {
+  if (threadIdx.x < G::KP) {
     s_beta[threadIdx.x] = threadIdx.x < k ? S->beta[threadIdx.x] : 0.0;
     s_active[threadIdx.x] = threadIdx.x < k ? S->active[threadIdx.x] : 0;
   }
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_direction(int64_t n, int k, con
     G::load(P, u, n, k, p);
 #pragma unroll
     for (int w = 0; w < G::W; ++w)
-      if (s_active[G::col(w)]) p[w] = fma(s_beta[G::col(w)], p[w], r[w]);
+      if (s_active[G::gcol(u, w)]) p[w] = fma(s_beta[G::gcol(u, w)], p[w], r[w]);
     G::store(P, u, n, k, p);
   }
   __syncthreads();
@@ -352,11 +359,11 @@ __global__ void __launch_bounds__(kThreads) k_lz_norm(int64_t n, int k, const do
     double v[G::W];
     G::load(V0, u, n, k, v);
 #pragma unroll
-    for (int w = 0; w < G::W; ++w) acc[0][G::col(w)] = fma(v[w], v[w], acc[0][G::col(w)]);
+    for (int w = 0; w < G::W; ++w) acc[0][G::acol(w)] = fma(v[w], v[w], acc[0][G::acol(w)]);
   }
-  if (!publish_partials<G::KC, 1>(acc, partial, counter, k)) return;
-  __shared__ double tot[1][G::KC];
-  finish_partials<G::KC, 1>(partial, k, tot);
+  if (!publish_partials<G, 1>(acc, partial, counter, k)) return;
+  __shared__ double tot[1][G::KP];
+  finish_partials<G::KP, 1>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     const double b = sqrt(tot[0][q]);
@@ -374,9 +381,9 @@ template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads) k_lz_scale(int64_t n, int k, const double* __restrict__ src,
                                                        double* dst, double* zero_out, const LzScalars* S) {
   using G = Seg<K, MODE>;
-  __shared__ double s_b[G::KC];
-  __shared__ int s_live[G::KC];
-  if (threadIdx.x < G::KC) {
+  __shared__ double s_b[G::KP];
+  __shared__ int s_live[G::KP];
+  if (threadIdx.x < G::KP) {
     s_b[threadIdx.x] = threadIdx.x < k ? S->inv_b[threadIdx.x] : 0.0;
     s_live[threadIdx.x] = threadIdx.x < k ? S->live[threadIdx.x] : 0;
   }
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_lz_scale(int64_t n, int k, const d
     double v[G::W];
     G::load(src, u, n, k, v);
 #pragma unroll
-    for (int w = 0; w < G::W; ++w) v[w] = s_live[G::col(w)] ? v[w] * s_b[G::col(w)] : 0.0;
+    for (int w = 0; w < G::W; ++w) v[w] = s_live[G::gcol(u, w)] ? v[w] * s_b[G::gcol(u, w)] : 0.0;
     G::store(dst, u, n, k, v);
     if (zero_out) {
 #pragma unroll
@@ -401,8 +408,8 @@ __global__ void __launch_bounds__(kThreads) k_lz_alpha(int64_t n, int k, double*
                                                        const double* __restrict__ v_prev, double* partial,
                                                        uint32_t* counter, LzScalars* S, double* alpha_out) {
   using G = Seg<K, MODE>;
-  __shared__ double s_b[G::KC];
-  if (threadIdx.x < G::KC) s_b[threadIdx.x] = threadIdx.x < k ? S->b_prev[threadIdx.x] : 0.0;
+  __shared__ double s_b[G::KP];
+  if (threadIdx.x < G::KP) s_b[threadIdx.x] = threadIdx.x < k ? S->b_prev[threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1][G::KC];
 #pragma unroll
@@ -414,14 +421,14 @@ __global__ void __launch_bounds__(kThreads) k_lz_alpha(int64_t n, int k, double*
     G::load(v_prev, u, n, k, vp);
 #pragma unroll
     for (int w = 0; w < G::W; ++w) {
-      w_[w] = fma(-s_b[G::col(w)], vp[w], w_[w]);
-      acc[0][G::col(w)] = fma(w_[w], vv[w], acc[0][G::col(w)]);
+      w_[w] = fma(-s_b[G::gcol(u, w)], vp[w], w_[w]);
+      acc[0][G::acol(w)] = fma(w_[w], vv[w], acc[0][G::acol(w)]);
     }
     G::store(W, u, n, k, w_);
   }
-  if (!publish_partials<G::KC, 1>(acc, partial, counter, k)) return;
-  __shared__ double tot[1][G::KC];
-  finish_partials<G::KC, 1>(partial, k, tot);
+  if (!publish_partials<G, 1>(acc, partial, counter, k)) return;
+  __shared__ double tot[1][G::KP];
+  finish_partials<G::KP, 1>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     const double a = S->live[q] ? tot[0][q] : 0.0;
@@ -439,8 +446,8 @@ __global__ void __launch_bounds__(kThreads) k_lz_beta(int64_t n, int k, double* 
                                                       double* partial, uint32_t* counter, LzScalars* S,
                                                       double* beta_out) {
   using G = Seg<K, MODE>;
-  __shared__ double s_a[G::KC];
-  if (threadIdx.x < G::KC) s_a[threadIdx.x] = threadIdx.x < k ? S->alpha[threadIdx.x] : 0.0;
+  __shared__ double s_a[G::KP];
+  if (threadIdx.x < G::KP) s_a[threadIdx.x] = threadIdx.x < k ? S->alpha[threadIdx.x] : 0.0;
   __syncthreads();
   double acc[1][G::KC];
 #pragma unroll
@@ -451,14 +458,14 @@ __global__ void __launch_bounds__(kThreads) k_lz_beta(int64_t n, int k, double* 
     G::load(v, u, n, k, vv);
 #pragma unroll
     for (int w = 0; w < G::W; ++w) {
-      w_[w] = fma(-s_a[G::col(w)], vv[w], w_[w]);
-      acc[0][G::col(w)] = fma(w_[w], w_[w], acc[0][G::col(w)]);
+      w_[w] = fma(-s_a[G::gcol(u, w)], vv[w], w_[w]);
+      acc[0][G::acol(w)] = fma(w_[w], w_[w], acc[0][G::acol(w)]);
     }
     G::store(W, u, n, k, w_);
   }
-  if (!publish_partials<G::KC, 1>(acc, partial, counter, k)) return;
-  __shared__ double tot[1][G::KC];
-  finish_partials<G::KC, 1>(partial, k, tot);
+  if (!publish_partials<G, 1>(acc, partial, counter, k)) return;
+  __shared__ double tot[1][G::KP];
+  finish_partials<G::KP, 1>(partial, k, tot);
   if (threadIdx.x < k) {
     const int q = threadIdx.x;
     const double b = S->live[q] ? sqrt(tot[0][q]) : 0.0;
@@ -473,15 +480,16 @@ __global__ void __launch_bounds__(kThreads) k_lz_beta(int64_t n, int k, double* 
 #undef UNIT_LOOP
 
 // ---------------------------------------------------------------- dispatch
-// k = 1 -> pairs; k = 2, 4, 8, 16 -> vector rows; other k -> scalar rows.
+// k = 1 -> pairs; k = 2, 4 -> vector rows; k = 8, 16 -> 4-column groups;
+// other k -> scalar rows.
 template <template <int, int> class F, typename... Args>
 static cudaError_t by_k(int k, Args... args) {
   switch (k) {
     case 1: return F<1, PAIRS>::run(args...);
     case 2: return F<2, VROWS>::run(args...);
     case 4: return F<4, VROWS>::run(args...);
-    case 8: return F<8, VROWS>::run(args...);
-    case 16: return F<16, VROWS>::run(args...);
+    case 8: return F<8, VGROUPS>::run(args...);
+    case 16: return F<16, VGROUPS>::run(args...);
     default: break;
   }
   if (k <= 4) return F<4, ROWS>::run(args...);
@@ -508,12 +516,14 @@ SOLVER_LAUNCHER(LLzAlpha, k_lz_alpha)
 SOLVER_LAUNCHER(LLzBeta, k_lz_beta)
 #undef SOLVER_LAUNCHER
 
-// Resident CTAs per SM of the heaviest vector kernel (sets the fixed grid:
-// every kernel then runs in one wave).
+// Resident CTAs per SM of each vector kernel (the CG kernels come first,
+// then the Lanczos ones, four each).
+enum { KI_CG_INIT = 0, KI_CG_ALPHA, KI_CG_UPDATE, KI_CG_DIRECTION, KI_LZ_NORM, KI_LZ_SCALE, KI_LZ_ALPHA,
+       KI_LZ_BETA, KI_COUNT };
+
 template <int K, int MODE>
 struct LOccupancy {
-  static cudaError_t run(int* out) {
-    int o[8];
+  static cudaError_t run(int* o) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 0, k_cg_init<K, MODE>, kThreads, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 1, k_cg_alpha<K, MODE>, kThreads, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 2, k_cg_update<K, MODE>, kThreads, 0);
@@ -522,9 +532,6 @@ struct LOccupancy {
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 5, k_lz_scale<K, MODE>, kThreads, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 6, k_lz_alpha<K, MODE>, kThreads, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o + 7, k_lz_beta<K, MODE>, kThreads, 0);
-    int m = o[0];
-    for (int i = 1; i < 8; ++i) m = o[i] < m ? o[i] : m;
-    *out = m;
     return e;
   }
 };
@@ -537,7 +544,7 @@ struct spmv_solver {
   spmv_handle A = nullptr;
   int device = 0, k = 0;
   int64_t n = 0;
-  unsigned grid = 0;
+  unsigned grid[KI_COUNT] = {};    // one-wave grid of each vector kernel
   double *buf[3] = {nullptr, nullptr, nullptr};  // CG: R, P, Q; Lanczos: v_prev, v, W
   double* partial = nullptr;
   uint32_t* counter = nullptr;
@@ -586,13 +593,13 @@ spmv_status cg_iteration(spmv_solver* S, double* X, cudaStream_t s) {
   double *R = S->buf[0], *P = S->buf[1], *Q = S->buf[2];
   spmv_status st = spmv_apply_block(S->A, P, S->k, S->k, Q, S->k, s);
   if (st != SPMV_OK) return st;
-  cudaError_t e = by_k<LCgAlpha>(S->k, S->grid, s, S->n, S->k, (const double*)P, (const double*)Q, S->partial,
-                                 S->counter, S->cg);
+  cudaError_t e = by_k<LCgAlpha>(S->k, S->grid[KI_CG_ALPHA], s, S->n, S->k, (const double*)P, (const double*)Q,
+                                 S->partial, S->counter, S->cg);
   if (e == cudaSuccess)
-    e = by_k<LCgUpdate>(S->k, S->grid, s, S->n, S->k, X, R, (const double*)P, (const double*)Q, S->partial,
-                        S->counter, S->cg);
+    e = by_k<LCgUpdate>(S->k, S->grid[KI_CG_UPDATE], s, S->n, S->k, X, R, (const double*)P, (const double*)Q,
+                        S->partial, S->counter, S->cg);
   if (e == cudaSuccess)
-    e = by_k<LCgDirection>(S->k, S->grid, s, S->n, S->k, (const double*)R, P, S->counter, S->cg);
+    e = by_k<LCgDirection>(S->k, S->grid[KI_CG_DIRECTION], s, S->n, S->k, (const double*)R, P, S->counter, S->cg);
   return e == cudaSuccess ? SPMV_OK : cuda_fail(e, "CG kernel launch");
 }
 }  // namespace
@@ -616,15 +623,25 @@ spmv_status spmv_solver_create(spmv_handle A, int32_t k, spmv_solver_handle* out
   SolverDeviceGuard g(S->device);
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
-  int per_sm = 0;
-  if (e == cudaSuccess) e = by_k<LOccupancy>(k, &per_sm);
-  per_sm = per_sm < 1 ? 1 : (per_sm > kSolverCtasPerSm ? kSolverCtasPerSm : per_sm);
+  // The kernels of one method (CG: 4, Lanczos: 4) share the one-wave grid of the
+  // heaviest of them (measured: 1-2 % faster iterations at k >= 4 than a grid per
+  // kernel, and 2 % faster at k = 1 than one grid for all 8 kernels).
+  int per_sm[KI_COUNT] = {};
+  if (e == cudaSuccess) e = by_k<LOccupancy>(k, per_sm);
   const int64_t want = (S->n + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * per_sm;
-  S->grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+  unsigned max_grid = 1;
+  for (int m0 = 0; m0 < KI_COUNT; m0 += 4) {
+    int r = kSolverCtasPerSm;
+    for (int i = m0; i < m0 + 4; ++i) r = per_sm[i] < r ? per_sm[i] : r;
+    r = r < 1 ? 1 : r;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * r;
+    const unsigned g = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+    for (int i = m0; i < m0 + 4; ++i) S->grid[i] = g;
+    max_grid = g > max_grid ? g : max_grid;
+  }
   const size_t vec = sizeof(double) * (size_t)(S->n > 0 ? S->n : 1) * (size_t)k;
   for (int b = 0; b < 3 && e == cudaSuccess; ++b) e = cudaMalloc(&S->buf[b], vec);
-  if (e == cudaSuccess) e = cudaMalloc(&S->partial, sizeof(double) * S->grid * 2 * kMaxCols);
+  if (e == cudaSuccess) e = cudaMalloc(&S->partial, sizeof(double) * max_grid * 2 * kMaxCols);
   if (e == cudaSuccess) e = cudaMalloc(&S->counter, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(S->counter, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&S->cg, sizeof(CgScalars));
@@ -668,8 +685,8 @@ spmv_status spmv_cg_solve(spmv_solver_handle S, const double* B_dev, double* X_d
     // R = B - A X0, P = R, scalars
     spmv_status st = spmv_apply_block(S->A, X_dev, S->k, S->k, S->buf[2], S->k, s);
     if (st != SPMV_OK) return st;
-    cudaError_t e = by_k<LCgInit>(S->k, S->grid, s, S->n, S->k, B_dev, (const double*)S->buf[2], S->buf[0],
-                                  S->buf[1], S->partial, S->counter, S->cg, rtol * rtol);
+    cudaError_t e = by_k<LCgInit>(S->k, S->grid[KI_CG_INIT], s, S->n, S->k, B_dev, (const double*)S->buf[2],
+                                  S->buf[0], S->buf[1], S->partial, S->counter, S->cg, rtol * rtol);
     if (e != cudaSuccess) return cuda_fail(e, "CG init launch");
     const int steps = check_every < max_iter ? check_every : (max_iter > 0 ? max_iter : 1);
     const uint64_t gen = plan_generation(S->A);
@@ -760,22 +777,22 @@ spmv_status spmv_lanczos(spmv_solver_handle S, const double* V0_dev, int32_t m, 
   double* a_out = S->lz_out;
   double* b_out = S->lz_out + (size_t)m * kMaxCols;
   double *v_prev = S->buf[0], *v = S->buf[1], *W = S->buf[2];
-  cudaError_t e = by_k<LLzNorm>(k, S->grid, s, S->n, k, V0_dev, S->partial, S->counter, S->lz);
+  cudaError_t e = by_k<LLzNorm>(k, S->grid[KI_LZ_NORM], s, S->n, k, V0_dev, S->partial, S->counter, S->lz);
   if (e == cudaSuccess)
-    e = by_k<LLzScale>(k, S->grid, s, S->n, k, V0_dev, v, v_prev, (const LzScalars*)S->lz);
+    e = by_k<LLzScale>(k, S->grid[KI_LZ_SCALE], s, S->n, k, V0_dev, v, v_prev, (const LzScalars*)S->lz);
   if (e == cudaSuccess) e = cudaMemsetAsync(S->lz->b_prev, 0, sizeof(double) * kMaxCols, s);
   if (e != cudaSuccess) return cuda_fail(e, "Lanczos start");
   for (int j = 0; j < m; ++j) {
     spmv_status st = spmv_apply_block(S->A, v, k, k, W, k, s);
     if (st != SPMV_OK) return st;
-    e = by_k<LLzAlpha>(k, S->grid, s, S->n, k, W, (const double*)v, (const double*)v_prev, S->partial, S->counter,
-                       S->lz, a_out + (size_t)j * kMaxCols);
+    e = by_k<LLzAlpha>(k, S->grid[KI_LZ_ALPHA], s, S->n, k, W, (const double*)v, (const double*)v_prev, S->partial,
+                       S->counter, S->lz, a_out + (size_t)j * kMaxCols);
     if (e == cudaSuccess)
-      e = by_k<LLzBeta>(k, S->grid, s, S->n, k, W, (const double*)v, S->partial, S->counter, S->lz,
+      e = by_k<LLzBeta>(k, S->grid[KI_LZ_BETA], s, S->n, k, W, (const double*)v, S->partial, S->counter, S->lz,
                         b_out + (size_t)j * kMaxCols);
     // v_{j+1} = W / beta_j into the buffer of v_{j-1}, then rotate
     if (e == cudaSuccess)
-      e = by_k<LLzScale>(k, S->grid, s, S->n, k, (const double*)W, v_prev, (double*)nullptr,
+      e = by_k<LLzScale>(k, S->grid[KI_LZ_SCALE], s, S->n, k, (const double*)W, v_prev, (double*)nullptr,
                          (const LzScalars*)S->lz);
     if (e != cudaSuccess) return cuda_fail(e, "Lanczos kernel launch");
     double* t = v_prev;

@@ -91,10 +91,11 @@ def test_spmm_leading_dimensions(lib):
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("vname", ["SPMV_CRS_L1", "SPMV_CRS_STAGED", "SPMV_SELL"])
 def test_spmm_16_byte_and_scalar_paths_identical(lib, k, fp32, vname):
-    """A full contiguous, 16-byte aligned block of k = 8 or 16 columns takes
-    16-byte gathers and stores; the same product from blocks 8 bytes off
-    alignment (and every k = 2, 4 block) takes scalar accesses.  The
-    arithmetic is the same, so are the bits."""
+    """A full contiguous, 16-byte aligned block of k >= 2 columns takes the
+    column-split kernels (16-byte gathers and stores, several lanes per row
+    for k >= 8); the same product from blocks 8 bytes off alignment takes the
+    scalar thread-per-row accesses.  Each column's sum is formed in the same
+    order, so the bits are the same."""
     import torch
     A = case("powerlaw")
     B = gen.rhs_block(A.n_cols, k, seed=20 + k)
