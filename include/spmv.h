@@ -131,8 +131,9 @@ spmv_status spmv_apply_block(spmv_handle h, const double* B_dev, int32_t k, int6
 
 /* Local/halo split product with overlapped halo copy (Sec. 3.1 and 3.2 recast
  * for one GPU): on copy_stream, B_halo_pinned[0 : n_cols - h] is copied into
- * B_dev[h : n_cols] while the local kernel (entries with col < h) writes C on
- * main_stream; main_stream then waits for the copy and the halo kernel adds
+ * B_dev[h : n_cols] while the local kernel (entries with col < h; the plan's
+ * CRS variant, CRS_L1 for SELL and SYM plans) writes C on main_stream;
+ * main_stream then waits for the copy and the halo kernel adds
  * the entries with col >= h into C.  B_dev[0:h] must already hold the local
  * part.  Requires a plan built with halo_begin = h.  copy_stream may equal
  * main_stream (no overlap).  On return all work is enqueued; main_stream

@@ -507,7 +507,10 @@ spmv_status spmv_apply_split(spmv_handle h, double* B_dev, const double* B_halo_
                               cs));
     if (cs != ms) SPMV_CUDA(cudaEventRecord(h->ev_copy, cs));
   }
-  cudaError_t e = launch_crs_staged(h->local, f32, B_dev, 1, C_dev, 1, 1, false, h->status, ms);
+  // local pass: the plan's CRS kernel (SELL and SYM plans have no local copy in
+  // their format, so they run CRS_L1 here)
+  const int lv = h->variant >= SPMV_CRS_STAGED && h->variant <= SPMV_CRS_L32 ? h->variant : SPMV_CRS_L1;
+  cudaError_t e = run_variant(h, h->local, lv, B_dev, 1, C_dev, 1, 1, ms);
   if (e != cudaSuccess) return cuda_fail(e, "local kernel launch");
   if (nhalo > 0 && cs != ms) SPMV_CUDA(cudaStreamWaitEvent(ms, h->ev_copy, 0));
   e = launch_halo(h->halo, f32, B_dev, 1, C_dev, 1, 1, ms);

@@ -95,6 +95,20 @@ def test_split_product(lib, two_streams, fp32):
         assert_close(y, A, B)
 
 
+@pytest.mark.parametrize("vname", ["SPMV_CRS_STAGED", "SPMV_CRS_L1", "SPMV_CRS_L8", "SPMV_SELL", "SPMV_SYM"])
+def test_split_every_plan_variant(lib, vname):
+    """The local pass runs the plan's CRS kernel (CRS_L1 for SELL and SYM
+    plans); every choice gives the oracle's split product."""
+    A = gen.poisson3d_var(30)
+    h = A.n_cols - A.n_cols // 7
+    B = gen.uniform(A.n_cols, seed=11)
+    with lib.Plan.from_csr(A, halo_begin=h, variant=getattr(lib, vname), sell_sigma=64) as p:
+        y = run_split(lib, p, A, B, h)
+    ref = oracle.split_spmv(A.n_rows, oracle.split_build(A, h), B)
+    assert oracle.max_err_ratio(y, ref, oracle.abs_scale(A, B), TOL_FP64) <= 1.0
+    assert_close(y, A, B)
+
+
 def test_split_integer_exact(lib):
     A = gen.random_csr(5000, 5000, 0.002, 9, integer=True, empty_rows=0.1)
     h = 4100
