@@ -124,6 +124,53 @@ def test_poisson280_symmetric(lib, poisson280, fp32):
             assert np.all(np.abs(y1[rows] - 1e-3) <= TOL_FP64 * oracle.abs_scale(S, ones))
 
 
+@pytest.mark.parametrize("k", [2, 16])
+def test_poisson280_spmm_column_split(lib, poisson280, k):
+    """k right-hand sides on the full 3D Poisson workload through CRS_L1's
+    column-split kernel (a full 16-byte aligned block, as the benchmark's
+    SpMM section runs it), on sampled rows against the oracle's k-column loop;
+    the same product from a block 8 bytes off alignment (thread-per-row
+    scalar form) gives the same bits."""
+    import torch
+    A = poisson280
+    B = gen.rhs_block(A.n_cols, k, seed=k)
+    rows = sample_rows(A.n_rows, 6 + k, count=10_000)
+    with lib.Plan.from_csr(A) as p:
+        Bd = dev(B)
+        C = torch.full((A.n_rows, k), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply_block(Bd, C, k)
+        p.check()
+        y = host(C)
+        flat = torch.empty(A.n_rows * k + 1, dtype=torch.float64, device="cuda")
+        Co = flat[1:].view(A.n_rows, k)
+        p.apply_block(Bd, Co, k)
+        same = bool(torch.equal(C, Co))
+        del Bd, C, flat, Co
+    assert same
+    S = sub_csr(A, rows)
+    ref = oracle.spmm(S, B)
+    assert oracle.max_err_ratio(y[rows], ref, oracle.abs_scale(S, B), TOL_FP64) <= 1.0
+
+
+def test_eigen_full_sell_spmm_k4(lib):
+    """SELL-32-4096 with k = 4 on the eigenproblem-shaped workload (the column-split
+    SELL kernel), on sampled rows."""
+    import torch
+    A = gen.eigen_shaped()
+    k = 4
+    B = gen.rhs_block(A.n_cols, k, seed=3)
+    rows = sample_rows(A.n_rows, 9, count=10_000)
+    with lib.Plan.from_csr(A, variant=lib.SPMV_SELL, sell_sigma=4096) as p:
+        C = torch.full((A.n_rows, k), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply_block(dev(B), C, k)
+        p.check()
+        y = host(C)
+    assert not np.isnan(y).any()
+    S = sub_csr(A, rows)
+    ref = oracle.spmm(S, B)
+    assert oracle.max_err_ratio(y[rows], ref, oracle.abs_scale(S, B), TOL_FP64) <= 1.0
+
+
 def test_eigen_full_symmetric(lib):
     import torch
     A = gen.eigen_shaped()
