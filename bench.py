@@ -409,7 +409,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         line["ordering"] = ordering_forms(A, torch, spmv, pm, timer, stream, B, C, args.workload, args.form_steps)
     if "block" in groups and args.workload == "laplace2d_256":
         line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
-    if args.selector and k == 1:
+    if args.selector:
         line["selector"] = plan_selector(args, A, timer, stream, tr, spmv)
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -830,21 +830,25 @@ def batch_selector(args, As, batch, timer, stream, flops, spmv):
             "batch_gflops_default_policy": round(flops / t_def / 1e9, 1)}
 
 
+SELECTOR_KS = (1, 4, 16)   # right-hand-side counts of the plan selector's training samples
+
+
 def plan_selector(args, A, timer, stream, tr, spmv):
     """Cost model for single products: trained on generated matrices, picks the
     kernel for this workload; its time against the default kernel and the sweep."""
     import torch
     from paper_1101_0091_gb300 import selector as sel
     t0 = time.time()
-    train = sel.build_dataset(sel.training_matrices(args.selector_train, seed=1000, scale=0.25), "plan", stream)
+    train = sel.build_dataset(sel.training_matrices(args.selector_train, seed=1000, scale=0.25), "plan", stream,
+                              ks=SELECTOR_KS)
     cm = sel.train_model(train, len(sel.PLAN_VARIANTS))
     t_train = time.time() - t0
-    sweep = sel.sweep_plan(A, stream)
-    choice, _ = cm.select(spmv.features(A, 1))
+    sweep = sel.sweep_plan(A, stream, k=args.k)
+    choice, _ = cm.select(spmv.features(A, args.k))
     c = int(choice[0])
     names = [v[0] for v in sel.PLAN_VARIANTS]
-    return {"training_matrices": args.selector_train, "train_and_sweep_s": round(t_train, 1),
-            "chosen": names[c], "best_in_sweep": names[int(sweep.argmin())],
+    return {"training_matrices": args.selector_train, "training_k": list(SELECTOR_KS), "k": args.k,
+            "train_and_sweep_s": round(t_train, 1), "chosen": names[c], "best_in_sweep": names[int(sweep.argmin())],
             "gflops_chosen": round(tr.flops / sweep[c] / 1e9, 1),
             "gflops_default_" + names[sel.PLAN_DEFAULT]: round(tr.flops / sweep[sel.PLAN_DEFAULT] / 1e9, 1),
             "gflops_best": round(tr.flops / sweep.min() / 1e9, 1),

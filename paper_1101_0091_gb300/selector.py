@@ -3,7 +3,8 @@ kernels, the MLP cost model trained on them (forward, backward and Adam run in
 the library's CUDA kernels), and the regret of its choices.
 
 Two contexts share the code:
-* "plan":  single-matrix products, k = 1; the variants are the plan kernels
+* "plan":  single-matrix products of k columns (k is a feature; one sample
+           per matrix and k); the variants are the plan kernels
            (CRS_L1/L2/L4/L8/L32, CRS_STAGED, SELL-32 with sigma 1/256/4096).
 * "batch": members of a batched launch, k = 4; the variants are the batch row
            policies (fixed 1/2/4/8/32 lanes per row, adaptive, sorted).
@@ -52,17 +53,19 @@ def event_time(fn, stream, reps: int = 7, warm: int = 2) -> float:
 
 # ------------------------------------------------------------------- sweeps
 
-def sweep_plan(A, stream, reps: int = 7) -> np.ndarray:
-    """Seconds of one product with every plan variant (k = 1)."""
+def sweep_plan(A, stream, reps: int = 7, k: int = 1) -> np.ndarray:
+    """Seconds of one product of k columns with every plan variant."""
     torch = _torch()
-    B = torch.from_numpy(np.ones(A.n_cols)).cuda() if A.n_cols else torch.zeros(1, dtype=torch.float64).cuda()
-    C = torch.empty(max(A.n_rows, 1), dtype=torch.float64, device="cuda")
+    shape_b = (max(A.n_cols, 1),) if k == 1 else (max(A.n_cols, 1), k)
+    B = torch.ones(shape_b, dtype=torch.float64, device="cuda")
+    C = torch.empty((max(A.n_rows, 1),) if k == 1 else (max(A.n_rows, 1), k), dtype=torch.float64, device="cuda")
     stream.wait_stream(torch.cuda.current_stream())
     out = np.zeros(len(PLAN_VARIANTS))
     with Plan.from_csr(A) as p:
+        fn = (lambda: p.apply(B, C, stream)) if k == 1 else (lambda: p.apply_block(B, C, k, stream))
         for i, (_, vid, sigma) in enumerate(PLAN_VARIANTS):
             p.set_variant(vid, sigma)
-            out[i] = event_time(lambda: p.apply(B, C, stream), stream, reps)
+            out[i] = event_time(fn, stream, reps)
     return out
 
 
@@ -123,12 +126,16 @@ class Dataset:
     names: list = field(default_factory=list)
 
 
-def build_dataset(mats, context: str, stream, k: int = None) -> Dataset:
+def build_dataset(mats, context: str, stream, k: int = None, ks=None) -> Dataset:
+    """One sample per matrix and k (ks, default [k]; k defaults to 1 for the
+    plan context and 4 for the batch context)."""
     k = (1 if context == "plan" else 4) if k is None else k
+    ks = [k] if ks is None else list(ks)
     X, TT = [], []
     for A in mats:
-        X.append(features(A, k))
-        TT.append(sweep_plan(A, stream) if context == "plan" else sweep_batch(A, stream, k))
+        for kk in ks:
+            X.append(features(A, kk))
+            TT.append(sweep_plan(A, stream, k=kk) if context == "plan" else sweep_batch(A, stream, kk))
     times = np.array(TT)
     return Dataset(np.array(X), np.log(times), times)
 
