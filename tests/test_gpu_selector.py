@@ -103,3 +103,30 @@ def test_native_exhaustive_sweep(lib):
             p.autotune(Bd, C, [(lib.SPMV_SYM, 1)], reps=2)
         assert e.value.status == 6
         assert p.info().variant == cands[best][0]
+
+
+def test_selector_across_right_hand_side_counts(lib):
+    """Plan-context samples for several k (k is feature 33, log2 k): one sample
+    per matrix and k; a model trained on k = 1 and 4 picks, on held-out
+    matrices at k = 4, kernels whose total time beats the default's."""
+    import torch
+    from paper_1101_0091_gb300 import selector
+    stream = torch.cuda.Stream()
+    mats = selector.training_matrices(40, seed=2000, scale=0.2)
+    train = selector.build_dataset(mats, "plan", stream, ks=(1, 4))
+    assert train.X.shape == (2 * len(mats), 34) and train.times.shape == (2 * len(mats), len(selector.PLAN_VARIANTS))
+    assert np.array_equal(train.X[:, 33], np.tile([0.0, 2.0], len(mats)))
+    cm = selector.CostModel(len(selector.PLAN_VARIANTS), hidden=64, seed=0)
+    cm.fit(train, epochs=1500, lr=3e-3)
+    held = [gen.eigen_shaped(300_000, seed=17, window=1 << 18), gen.poisson3d_var(50, seed=19),
+            gen.powerlaw(120_000, seed=18, lmax=2000)]
+    test = selector.build_dataset(held, "plan", stream, k=4)
+    assert np.all(test.X[:, 33] == 2.0)
+    choice, _ = cm.select(test.X)
+    t_learned = test.times[np.arange(len(held)), choice].sum()
+    t_default = test.times[:, selector.PLAN_DEFAULT].sum()
+    names = [v[0] for v in selector.PLAN_VARIANTS]
+    print("k = 4 held-out: chosen", [names[c] for c in choice], "best", [names[c] for c in test.times.argmin(axis=1)],
+          "time ratio", t_learned / t_default)
+    assert t_learned <= t_default
+    assert selector.regret(test.times, choice)["total"] < 0.25
