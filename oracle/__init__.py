@@ -53,6 +53,7 @@ def _load():
             lib.oracle_crs_spmm.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, i64]
             lib.oracle_crs_spmm_f32val.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, i64]
             lib.oracle_abs_scale.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, i64]
+            lib.oracle_crs_spmm_dot2.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, i64]
             lib.oracle_sell_perm.argtypes = [i64, vp, i64, i64, vp, ctypes.POINTER(i64)]
             lib.oracle_sell_perm.restype = i64
             lib.oracle_sell_fill.argtypes = [i64, vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
@@ -105,6 +106,19 @@ def spmm(A, B, f32val: bool = False) -> np.ndarray:
     fn = _load().oracle_crs_spmm_f32val if f32val else _load().oracle_crs_spmm
     fn(A.n_rows, k, rp, ci, va, pB, k, C.ctypes.data, k)
     return C
+
+
+def spmm_dot2(A, B) -> np.ndarray:
+    """Row sums of A*B as if computed in twice the working precision (compensated
+    dot product, Ogita-Rump-Oishi Dot2); for attributing a failed parity check,
+    not a reference of the checks themselves."""
+    keep, (rp, ci, va) = _csr(A)
+    Bc, pB = _c(B, np.float64)
+    Bc2 = Bc.reshape(Bc.shape[0], -1)
+    k = Bc2.shape[1]
+    C = np.empty((A.n_rows, k), dtype=np.float64)
+    _load().oracle_crs_spmm_dot2(A.n_rows, k, rp, ci, va, pB, k, C.ctypes.data, k)
+    return C if Bc.ndim > 1 else C[:, 0]
 
 
 def abs_scale(A, B) -> np.ndarray:

@@ -66,6 +66,39 @@ void oracle_crs_spmm_f32val(int64_t n_rows, int64_t k, const int32_t* row_ptr,
   }
 }
 
+/* The same row sums evaluated as if in twice the working precision, used to
+ * attribute an error to one side when a parity check fails (it is not the
+ * reference of any check).  Compensated dot product in the manner of Ogita, Rump and Oishi
+ * (SIAM J. Sci. Comput. 26, 2005, "Dot2"): every product is split exactly into
+ * p + e with one fused multiply-add (e = fma(a, b, -p), the rounding error of
+ * p), the p are summed with Knuth's TwoSum, which yields each addition's
+ * rounding error exactly, and all error terms are added to the sum at the end.
+ * fma() is called explicitly; the file is compiled with -ffp-contract=off. */
+static void two_sum(double a, double b, double* s, double* t) {
+  const double x = a + b;
+  const double z = x - a;
+  *t = (a - (x - z)) + (b - z);
+  *s = x;
+}
+
+void oracle_crs_spmm_dot2(int64_t n_rows, int64_t k, const int32_t* row_ptr, const int32_t* col_idx,
+                          const double* val, const double* B, int64_t ldb, double* C, int64_t ldc) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    for (int64_t c = 0; c < k; ++c) {
+      double s = 0.0, err = 0.0;
+      for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+        const double a = val[j], b = B[(int64_t)col_idx[j] * ldb + c];
+        const double p = a * b;
+        const double e = fma(a, b, -p);
+        double t;
+        two_sum(s, p, &s, &t);
+        err = err + (t + e);
+      }
+      C[i * ldc + c] = s + err;
+    }
+  }
+}
+
 /* Error scale of the tolerance: S[i, c] = sum_j |val[j] * B[col_idx[j], c]|. */
 void oracle_abs_scale(int64_t n_rows, int64_t k, const int32_t* row_ptr, const int32_t* col_idx,
                       const double* val, const double* B, int64_t ldb, double* S, int64_t lds) {

@@ -206,3 +206,63 @@ def test_max_err_ratio_semantics():
     assert oracle.max_err_ratio([1.0], [1.0], [0.0], TOL) == 0.0
     assert oracle.max_err_ratio([1.0], [np.nextafter(1.0, 2.0)], [0.0], TOL) == float("inf")
     assert oracle.max_err_ratio([1.0 + 1e-14], [1.0], [1.0], TOL) == pytest.approx(0.1, rel=0.2)
+
+
+def test_dot2_cancellation_row():
+    """A row whose exact sum the plain loop loses completely: 1e16 + 1 - 1e16.
+    The compensated evaluation recovers it exactly; the plain loop gives 0."""
+    A = gen.CSR(1, 3, np.array([0, 3], np.int32), np.array([0, 1, 2], np.int32), np.array([1e16, 1.0, -1e16]))
+    B = np.ones(3)
+    assert oracle.spmv(A, B)[0] == 0.0
+    assert oracle.spmm_dot2(A, B)[0] == 1.0
+    # the rounding error of a product is kept too: (1 + 2^-30)^2 - 1 - 2^-29
+    e = 2.0 ** -30
+    A2 = gen.CSR(1, 3, np.array([0, 3], np.int32), np.array([0, 1, 2], np.int32), np.array([1.0 + e, -1.0, -2 * e]))
+    B2 = np.array([1.0 + e, 1.0, 1.0])
+    assert oracle.spmm_dot2(A2, B2)[0] == e * e          # exact: 2^-60
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dot2_within_its_error_bound(seed):
+    """Against exact rational sums on ill-conditioned random rows (terms that
+    cancel to a small fraction of sum|ab|): |dot2 - exact| <= u|exact| +
+    gamma_n^2 sum|ab| (Ogita, Rump, Oishi 2005), for every column of a block."""
+    rng = np.random.default_rng(300 + seed)
+    n, m, k = 40, 60, 3
+    rows = [rng.choice(m, size=int(rng.integers(1, 30)), replace=False) for _ in range(n)]
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    va = rng.standard_normal(len(ci)) * 10.0 ** rng.integers(-8, 9, len(ci))
+    A = gen.CSR(n, m, rp, ci, va)
+    B = rng.standard_normal((m, k))
+    got = oracle.spmm_dot2(A, B)
+    plain = oracle.spmm(A, B)
+    u = 2.0 ** -53
+    worse = 0
+    for c in range(k):
+        ex = exact_product(A, B[:, c])
+        for i in range(n):
+            L = int(rp[i + 1] - rp[i])
+            g = L * u / (1 - L * u)
+            s = sum(abs(Fraction(float(A.val[j])) * Fraction(float(B[A.col_idx[j], c])))
+                    for j in range(rp[i], rp[i + 1]))
+            bound = u * abs(ex[i]) + Fraction(g * g) * s
+            assert abs(Fraction(float(got[i, c])) - ex[i]) <= bound
+            worse += abs(Fraction(float(plain[i, c])) - ex[i]) > abs(Fraction(float(got[i, c])) - ex[i])
+    assert worse > 0   # the plain loop is measurably less accurate on these rows
+
+
+def test_failed_check_attribution_message():
+    """The message a failed GPU parity check carries: the worst entry and the
+    distances of both sides from the compensated evaluation (a perturbed copy
+    of the oracle's result stands in for a faulty kernel)."""
+    from gpu_util import attribution
+    A = gen.poisson3d_var(6)
+    B = gen.rhs_block(A.n_cols, 2, seed=1)
+    ref = oracle.spmm(A, B)
+    y = ref.copy()
+    y[17, 1] += 1e-6
+    msg = attribution(y, ref, A, B, TOL)
+    assert msg.startswith("worst entry (17, 1):")
+    assert "|y - oracle| = 1.000e-06" in msg and "|oracle - dot2| = " in msg
