@@ -11,7 +11,8 @@
 // sustains about two FMAs per SM clock, so the kernel does no shuffle
 // reductions at all for these rows.  A "warp" block holds up to 8 rows longer
 // than 64 entries, one warp per row: lanes stride the row with coalesced loads
-// and a 5-step xor-shuffle tree sums their partials.
+// and a 5-step xor-shuffle tree sums their partials.  A full, 16-byte aligned
+// block of K >= 8 columns splits each tile row's columns over K / 4 lanes.
 #include <mutex>
 
 #include "device.cuh"
@@ -120,12 +121,37 @@ __global__ void __launch_bounds__(kThreads)
     mbar_wait_bounded(&bar, 0, kWaitLimitNs);  // let the copies in flight land before exiting
     return;
   }
+  if constexpr (VEC && K >= 8) {
+    // a full block of K >= 8 columns: each row is shared by G = K / 4 lanes, lane c owning
+    // columns 4c .. 4c + 3 (two 16-byte gathers per entry, the G lanes of a row read one
+    // contiguous piece of its B row); the block's rows take G passes of 256 / G rows.  Each
+    // column's entries are summed in order, as in the thread-per-row form.
+    constexpr int G = K / 4, RPP = kThreads / G;
+    const int c0 = (tid % G) * 4;
+    for (int r = r0 + tid / G; r < r1; r += RPP) {
+      const int s0 = __ldg(row_ptr + r), s1 = __ldg(row_ptr + r + 1);
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = s0; j < s1; ++j) {
+        const double v = to_f64(sval[j - v_lo]);
+        const double2* b = reinterpret_cast<const double2*>(B + (int64_t)scol[j - c_lo] * ldb + c0);
+        const double2 x = __ldg(b), y = __ldg(b + 1);
+        a[0] = fma(v, x.x, a[0]);
+        a[1] = fma(v, x.y, a[1]);
+        a[2] = fma(v, y.x, a[2]);
+        a[3] = fma(v, y.y, a[3]);
+      }
+      double2* out = reinterpret_cast<double2*>(C + (int64_t)r * ldc + c0);
+      out[0] = make_double2(a[0], a[1]);
+      out[1] = make_double2(a[2], a[3]);
+    }
+    return;
+  }
   if (row >= r1) return;
 
   double acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0;
-  constexpr int NB = Batch<K>::value;
+  constexpr int NB = VEC ? 1 : Batch<K>::value;  // 16-byte gathers: one entry per step measured fastest
   for (int j = rs; j < re; j += NB) {
     double v[NB];
     const double* b[NB];
