@@ -509,6 +509,41 @@ spmv_status spmv_reorder_destroy(spmv_reorder_handle h);
 spmv_status spmv_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
                           int32_t k, double* out);
 
+/* ----------------------------------------------------------------------------
+ * Host-side format builders (no device use): the builders that spmv_create and
+ * spmv_set_variant run, on HOST CRS arrays (validated as in spmv_create:
+ * malformed CRS -> SPMV_ERR_CSR; val may be NULL only when nnz = 0).  Two-call
+ * pattern: with the first output array NULL a call returns only the sizes; a
+ * second call with arrays of those sizes (caller-owned) fills them.  The
+ * arrays are the ones spmv_sell_export / spmv_split_export / spmv_sym_export
+ * copy from a plan, byte for byte.
+ *
+ * SELL-C-sigma, C = 32 (Kreutzer et al. 2014; the CRS loop of Sec. 1.2 on a
+ * sliced, sorted, column-major form): sigma >= 1 (else SPMV_ERR_ARG).
+ *   perm int32[n_rows], chunk_ptr int64[n_chunks + 1], chunk_len int32[n_chunks],
+ *   sell_col int32[n_slots], sell_val float64[n_slots].
+ * Local/halo split at column h (Sec. 3.1): 0 <= h <= n_cols (else SPMV_ERR_ARG).
+ *   loc_row_ptr int32[n_rows + 1], loc_col int32[loc_nnz], loc_val float64[loc_nnz],
+ *   halo_rows int32[n_halo_rows], halo_row_ptr int32[n_halo_rows + 1],
+ *   halo_col int32[halo_nnz], halo_val float64[halo_nnz].
+ * Symmetric triangle (Sec. 1.3.1): the entries with col >= row of each row;
+ *   SPMV_ERR_UNSUPPORTED (reason in spmv_last_error) unless the matrix is
+ *   square and symmetric.  sym_row_ptr int32[n_rows + 1], sym_col int32[sym_nnz],
+ *   sym_val float64[sym_nnz].
+ * ------------------------------------------------------------------------- */
+spmv_status spmv_sell_build_host(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
+                                 const double* val, int32_t sigma, int64_t* n_chunks, int64_t* n_slots,
+                                 int32_t* perm, int64_t* chunk_ptr, int32_t* chunk_len, int32_t* sell_col,
+                                 double* sell_val);
+spmv_status spmv_split_build_host(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
+                                  const double* val, int64_t h, int64_t* loc_nnz, int64_t* n_halo_rows,
+                                  int64_t* halo_nnz, int32_t* loc_row_ptr, int32_t* loc_col, double* loc_val,
+                                  int32_t* halo_rows, int32_t* halo_row_ptr, int32_t* halo_col,
+                                  double* halo_val);
+spmv_status spmv_sym_build_host(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col_idx,
+                                const double* val, int64_t* sym_nnz, int32_t* sym_row_ptr, int32_t* sym_col,
+                                double* sym_val);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_bl
                        spmv_split_export, spmv_sym_export, spmv_features, spmv_set_tuning, spmv_get_tuning,
                        spmv_tuning, SPMV_VARIANT_AUTO, SPMV_CRS_STAGED, SPMV_CRS_L1, SPMV_CRS_L2,
                        SPMV_CRS_L4, SPMV_CRS_L8, SPMV_CRS_L16, SPMV_CRS_L32, SPMV_SELL, SPMV_SYM,
-                       SPMV_N_VARIANTS)
+                       SPMV_N_VARIANTS, spmv_sell_build_host, spmv_split_build_host, spmv_sym_build_host)
 
 from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV_BATCH_L1,  # noqa: F401,E402
                              SPMV_BATCH_L2, SPMV_BATCH_L4, SPMV_BATCH_L8, SPMV_BATCH_L32, SPMV_BATCH_N_POLICIES,
@@ -53,6 +53,58 @@ def features(A, k: int = 1) -> np.ndarray:
     ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
     out = np.empty(N_FEATURES, dtype=np.float64)
     spmv_features(A.n_rows, A.n_cols, rp.ctypes.data, ci.ctypes.data, k, out.ctypes.data)
+    return out
+
+
+def _host_csr(A):
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    return rp, ci, va
+
+
+def sell_build(A, sigma: int = 1) -> dict:
+    """spmv_sell_build_host: the SELL-32-sigma arrays of a host CRS matrix (no device)."""
+    rp, ci, va = _host_csr(A)
+    nc, ns = np.zeros(1, np.int64), np.zeros(1, np.int64)
+    args = (A.n_rows, A.n_cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, sigma, nc.ctypes.data,
+            ns.ctypes.data)
+    spmv_sell_build_host(*args, None, None, None, None, None)
+    out = {"perm": np.empty(A.n_rows, np.int32), "chunk_ptr": np.empty(int(nc[0]) + 1, np.int64),
+           "chunk_len": np.empty(int(nc[0]), np.int32), "sell_col": np.empty(int(ns[0]), np.int32),
+           "sell_val": np.empty(int(ns[0]), np.float64)}
+    spmv_sell_build_host(*args, *(out[k].ctypes.data for k in ("perm", "chunk_ptr", "chunk_len", "sell_col",
+                                                               "sell_val")))
+    return out
+
+
+def split_build(A, h: int) -> dict:
+    """spmv_split_build_host: the local/halo split arrays at column h (no device)."""
+    rp, ci, va = _host_csr(A)
+    sz = np.zeros(3, np.int64)
+    args = (A.n_rows, A.n_cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, h, sz[0:].ctypes.data,
+            sz[1:].ctypes.data, sz[2:].ctypes.data)
+    spmv_split_build_host(*args, None, None, None, None, None, None, None)
+    nl, nh, hn = (int(x) for x in sz)
+    out = {"loc_row_ptr": np.empty(A.n_rows + 1, np.int32), "loc_col": np.empty(nl, np.int32),
+           "loc_val": np.empty(nl, np.float64), "halo_rows": np.empty(nh, np.int32),
+           "halo_row_ptr": np.empty(nh + 1, np.int32), "halo_col": np.empty(hn, np.int32),
+           "halo_val": np.empty(hn, np.float64)}
+    spmv_split_build_host(*args, *(out[k].ctypes.data for k in ("loc_row_ptr", "loc_col", "loc_val", "halo_rows",
+                                                                "halo_row_ptr", "halo_col", "halo_val")))
+    return out
+
+
+def sym_build(A) -> dict:
+    """spmv_sym_build_host: the stored upper triangle of a symmetric host CRS matrix
+    (raises SpmvError SPMV_ERR_UNSUPPORTED if A is not symmetric; no device)."""
+    rp, ci, va = _host_csr(A)
+    nz = np.zeros(1, np.int64)
+    args = (A.n_rows, A.n_cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, nz.ctypes.data)
+    spmv_sym_build_host(*args, None, None, None)
+    out = {"row_ptr": np.empty(A.n_rows + 1, np.int32), "col": np.empty(int(nz[0]), np.int32),
+           "val": np.empty(int(nz[0]), np.float64)}
+    spmv_sym_build_host(*args, out["row_ptr"].ctypes.data, out["col"].ctypes.data, out["val"].ctypes.data)
     return out
 
 

@@ -68,6 +68,10 @@ _SIGS = {
     "spmv_select": ([_vp, _vp, _i32, _vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_autotune": ([_vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp], ctypes.c_int),
     "spmv_features": ([_i64, _i64, _vp, _vp, _i32, _vp], ctypes.c_int),
+    "spmv_sell_build_host": ([_i64, _i64, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_split_build_host": ([_i64, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                              ctypes.c_int),
+    "spmv_sym_build_host": ([_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -162,6 +166,23 @@ def spmv_sym_export(h, row_ptr: int, col: int, val: int) -> None:
 
 def spmv_features(n_rows: int, n_cols: int, row_ptr: int, col_idx: int, k: int, out: int) -> None:
     _check(load().spmv_features(n_rows, n_cols, row_ptr, col_idx, k, out))
+
+
+def spmv_sell_build_host(n_rows, n_cols, row_ptr, col_idx, val, sigma, n_chunks, n_slots, perm, chunk_ptr,
+                         chunk_len, sell_col, sell_val) -> None:
+    _check(load().spmv_sell_build_host(n_rows, n_cols, row_ptr, col_idx, val, sigma, n_chunks, n_slots, perm,
+                                       chunk_ptr, chunk_len, sell_col, sell_val))
+
+
+def spmv_split_build_host(n_rows, n_cols, row_ptr, col_idx, val, h, loc_nnz, n_halo_rows, halo_nnz, loc_row_ptr,
+                          loc_col, loc_val, halo_rows, halo_row_ptr, halo_col, halo_val) -> None:
+    _check(load().spmv_split_build_host(n_rows, n_cols, row_ptr, col_idx, val, h, loc_nnz, n_halo_rows, halo_nnz,
+                                        loc_row_ptr, loc_col, loc_val, halo_rows, halo_row_ptr, halo_col, halo_val))
+
+
+def spmv_sym_build_host(n_rows, n_cols, row_ptr, col_idx, val, sym_nnz, sym_row_ptr, sym_col, sym_val) -> None:
+    _check(load().spmv_sym_build_host(n_rows, n_cols, row_ptr, col_idx, val, sym_nnz, sym_row_ptr, sym_col,
+                                      sym_val))
 
 
 class spmv_tuning(ctypes.Structure):
