@@ -34,7 +34,9 @@ __device__ __forceinline__ void prefetch_rows(int64_t f0, int64_t rows, int64_t 
   }
 }
 
-template <typename VT, int L, int K>
+// VEC (L > 1, a full block of K >= 2 columns with 16-byte aligned B rows): each
+// entry's K values are gathered with K / 2 16-byte loads instead of K 8-byte ones.
+template <typename VT, int L, int K, bool VEC>
 __global__ void __launch_bounds__(kThreads, (K == 1 ? 8 : 1))
     k_crs_lanes(int64_t n_rows, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
                 const int32_t* __restrict__ col, const VT* __restrict__ val, const double* __restrict__ B,
@@ -69,10 +71,21 @@ __global__ void __launch_bounds__(kThreads, (K == 1 ? 8 : 1))
       b[u] = B + (int64_t)(L >= 8 ? ldcs(col + jj) : ldg(col + jj)) * ldb;
     }
     double gv[NB][K];
+    if constexpr (VEC) {
 #pragma unroll
-    for (int u = 0; u < NB; ++u)
+      for (int u = 0; u < NB; ++u)
 #pragma unroll
-      for (int q = 0; q < K; ++q) gv[u][q] = (j + u * L < re && q < k) ? __ldg(b[u] + q) : 0.0;
+        for (int q = 0; q < K; q += 2) {
+          const double2 x = j + u * L < re ? __ldg(reinterpret_cast<const double2*>(b[u] + q)) : make_double2(0.0, 0.0);
+          gv[u][q] = x.x;
+          gv[u][q + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) gv[u][q] = (j + u * L < re && q < k) ? __ldg(b[u] + q) : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -153,8 +166,16 @@ static cudaError_t launch_lanes_t(int64_t n_rows, const int32_t* rows, const int
   }
   const int64_t rows_per_cta = kThreads / L;
   const int64_t grid = (n_rows + rows_per_cta - 1) / rows_per_cta;
-  k_crs_lanes<VT, L, K><<<(unsigned)grid, kThreads, 0, s>>>(n_rows, rows, row_ptr, col, val, B, ldb, C, ldc, k,
-                                                             acc ? 1 : 0, pf);
+  if constexpr (L > 1 && K >= 2) {
+    // several lanes per row on a full block with 16-byte aligned B rows: 16-byte gathers
+    if (k == K && ldb % 2 == 0 && (((uintptr_t)B) & 15) == 0) {
+      k_crs_lanes<VT, L, K, true><<<(unsigned)grid, kThreads, 0, s>>>(n_rows, rows, row_ptr, col, val, B, ldb, C,
+                                                                        ldc, k, acc ? 1 : 0, pf);
+      return cudaGetLastError();
+    }
+  }
+  k_crs_lanes<VT, L, K, false><<<(unsigned)grid, kThreads, 0, s>>>(n_rows, rows, row_ptr, col, val, B, ldb, C,
+                                                                     ldc, k, acc ? 1 : 0, pf);
   return cudaGetLastError();
 }
 

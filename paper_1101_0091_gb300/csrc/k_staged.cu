@@ -19,7 +19,7 @@
 
 namespace spmv {
 
-template <typename VT, int K>
+template <typename VT, int K, bool VEC>
 __device__ __forceinline__ void row_warp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                          const VT* __restrict__ val, int row, const double* __restrict__ B,
                                          int64_t ldb, double* __restrict__ C, int64_t ldc, int k,
@@ -32,9 +32,18 @@ __device__ __forceinline__ void row_warp(const int32_t* __restrict__ row_ptr, co
   for (int j = rs + lane; j < re; j += 32) {
     const double v = to_f64(ldcs(val + j));
     const double* b = B + (int64_t)ldcs(col + j) * ldb;
+    if constexpr (VEC) {  // k == K >= 2, 16-byte aligned rows of B
 #pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+      for (int q = 0; q < K; q += 2) {
+        const double2 x = __ldg(reinterpret_cast<const double2*>(b + q));
+        acc[q] = fma(v, x.x, acc[q]);
+        acc[q + 1] = fma(v, x.y, acc[q + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (q < k) acc[q] = fma(v, __ldg(b + q), acc[q]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = warp_sum_xor(acc[q], 32);
@@ -85,7 +94,7 @@ __global__ void __launch_bounds__(kThreads)
 
   if (e0 & kBlockWarpFlag) {  // block of long rows: one warp per row
     const int row = r0 + (tid >> 5);
-    if (row < r1) row_warp<VT, K>(row_ptr, col, val, row, B, ldb, C, ldc, k, accumulate);
+    if (row < r1) row_warp<VT, K, VEC>(row_ptr, col, val, row, B, ldb, C, ldc, k, accumulate);
     return;
   }
 
@@ -184,14 +193,14 @@ __global__ void __launch_bounds__(kThreads)
         if (j + u < re && q < k) acc[q] = fma(v[u], g[u][q], acc[q]);
   }
   double* out = C + (int64_t)row * ldc;
-  if (VEC) {
+  if constexpr (VEC) {
 #pragma unroll
     for (int q = 0; q < K; q += 2) reinterpret_cast<double2*>(out)[q / 2] = make_double2(acc[q], acc[q + 1]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int q = 0; q < K; ++q)
-    if (q < k) out[q] = accumulate ? out[q] + acc[q] : acc[q];
+    for (int q = 0; q < K; ++q)
+      if (q < k) out[q] = accumulate ? out[q] + acc[q] : acc[q];
+  }
 }
 
 template <typename VT, int K, bool VEC>

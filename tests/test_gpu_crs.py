@@ -89,12 +89,12 @@ def test_spmm_leading_dimensions(lib):
 
 @pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("fp32", [False, True])
-@pytest.mark.parametrize("vname", ["SPMV_CRS_L1", "SPMV_CRS_STAGED", "SPMV_SELL"])
+@pytest.mark.parametrize("vname", ["SPMV_CRS_L1", "SPMV_CRS_STAGED", "SPMV_SELL", "SPMV_CRS_L4", "SPMV_CRS_L32"])
 def test_spmm_16_byte_and_scalar_paths_identical(lib, k, fp32, vname):
     """A full contiguous, 16-byte aligned block of k >= 2 columns takes the
-    column-split kernels (16-byte gathers and stores, several lanes per row
-    for k >= 8); the same product from blocks 8 bytes off alignment takes the
-    scalar thread-per-row accesses.  Each column's sum is formed in the same
+    16-byte paths (the column-split kernels of CRS_L1, STAGED and SELL; 16-byte
+    gathers in the L-lanes kernels); the same product from blocks 8 bytes off
+    alignment takes scalar accesses.  Each column's sum is formed in the same
     order, so the bits are the same."""
     import torch
     A = case("powerlaw")
