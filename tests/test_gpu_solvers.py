@@ -29,10 +29,12 @@ def run_cg(lib, A, B, X0=None, variant=None, **kw):
         return host(Xd), it, rr, summ
 
 
-@pytest.mark.parametrize("k", [1, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8, 13, 16])
 def test_cg_fixed_iterations_match_oracle(lib, k):
     """rtol = 0: every column runs all iterations; the iterate and R.R follow
-    the oracle's (different rounding: FMA and reduction order)."""
+    the oracle's (different rounding: FMA and reduction order).  k covers every
+    way the vector kernels walk a block: pairs (1), rows (2, 4), 4-column groups
+    (8, 16) and masked scalar rows (3, 6, 13)."""
     A = gen.poisson3d_var(12)
     B = gen.rhs_block(A.n_cols, k, seed=k) if k > 1 else gen.uniform(A.n_cols, seed=1).reshape(-1, 1)
     for iters in (1, 5, 30):
@@ -71,6 +73,24 @@ def test_cg_columns_freeze_and_zero_rhs(lib):
         assert rel(X[:, c], Xo[:, c]) < 1e-7
 
 
+def test_cg_columns_freeze_in_column_groups(lib):
+    """k = 8 (4-column groups): zero, fast and slow columns in one group freeze
+    independently at the oracle's iteration counts."""
+    A = gen.poisson3d_var(10)
+    rng = np.random.default_rng(6)
+    cols = [np.zeros(A.n_rows), rng.standard_normal(A.n_rows), np.full(A.n_rows, 1e-3),
+            rng.standard_normal(A.n_rows), np.zeros(A.n_rows), np.full(A.n_rows, -2e-3),
+            rng.standard_normal(A.n_rows), rng.standard_normal(A.n_rows)]
+    B = np.stack(cols, 1)
+    X, it, rr, summ = run_cg(lib, A, B, max_iter=500, rtol=1e-8, check_every=5)
+    Xo, info = osol.cg(A, B, max_iter=500, rtol=1e-8)
+    assert it[0] == 0 and it[4] == 0 and np.all(X[:, [0, 4]] == 0)
+    assert np.all(np.abs(it.astype(int) - info["iterations"].astype(int)) <= 1)
+    assert summ.converged == 8
+    for c in (1, 2, 3, 5, 6, 7):
+        assert rel(X[:, c], Xo[:, c]) < 1e-7
+
+
 def test_cg_initial_guess(lib):
     A = gen.poisson3d_var(10)
     B = gen.rhs_block(A.n_cols, 2, seed=3)
@@ -97,12 +117,13 @@ def test_cg_deterministic_and_graph_eager_identical(lib):
     val = A.val.copy()
     val[d] += s
     A = gen.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, val)
-    B = gen.rhs_block(A.n_cols, 2, seed=5)
-    runs = [run_cg(lib, A, B, max_iter=37, rtol=0.0, check_every=ce)[0] for ce in (1, 7, 37, 100, 7)]
-    for r in runs[1:]:
-        assert np.array_equal(r, runs[0])
-    Xo, _ = osol.cg(A, B, max_iter=37, rtol=0.0)
-    assert rel(runs[0], Xo) < 1e-10
+    for k in (2, 16):
+        B = gen.rhs_block(A.n_cols, k, seed=5)
+        runs = [run_cg(lib, A, B, max_iter=37, rtol=0.0, check_every=ce)[0] for ce in (1, 7, 37, 100, 7)]
+        for r in runs[1:]:
+            assert np.array_equal(r, runs[0])
+        Xo, _ = osol.cg(A, B, max_iter=37, rtol=0.0)
+        assert rel(runs[0], Xo) < 1e-10
 
 
 @pytest.mark.parametrize("variant", ["SPMV_CRS_STAGED", "SPMV_CRS_L4", "SPMV_SELL", "SPMV_SYM"])
@@ -140,7 +161,7 @@ def test_solver_argument_errors(lib):
             assert "aligned" in str(e.value)
 
 
-@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 16])
 def test_lanczos_matches_oracle(lib, k):
     import torch
     A = gen.eigen_shaped(20_000, window=1 << 12)
