@@ -385,7 +385,7 @@ spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32
 spmv_status spmv_select(spmv_handle h, spmv_model_handle m, int32_t k, const int32_t* variants,
                         const int32_t* sigmas, int32_t* choice, void* stream);
 
-/* Exhaustive timed sweep, the fallback of the cost model and the judge of its
+/* Exhaustive timed sweep, the fallback of the cost model and the measure of its
  * regret: for each candidate (variants[i], sigmas[i]), i < n, the product of
  * k right-hand sides B_dev -> C_dev (layout as spmv_apply_block) is run once
  * untimed and then `reps` times between CUDA events on `stream`; the plan
