@@ -710,8 +710,13 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     rows = sum(A.n_rows for A in As)
     flops = 8 * nnz
     plans = [spmv.Plan.from_csr(A) for A in As]
-    Bs = [torch.from_numpy(B).cuda() for B in Bhs]
-    Cs = [torch.empty((A.n_rows, 4), dtype=torch.float64, device="cuda") for A in As]
+    # every member's B and C is a view of one device allocation per operand (members back to
+    # back, each 32-byte aligned), so the host path moves each operand in one copy
+    nb, nc = [A.n_cols * 4 for A in As], [A.n_rows * 4 for A in As]
+    Bflat = torch.from_numpy(np.concatenate([B.ravel() for B in Bhs])).cuda()
+    Cflat = torch.empty(sum(nc), dtype=torch.float64, device="cuda")
+    Bs = [v.view(A.n_cols, 4) for v, A in zip(torch.split(Bflat, nb), As)]
+    Cs = [v.view(A.n_rows, 4) for v, A in zip(torch.split(Cflat, nc), As)]
     stream.wait_stream(torch.cuda.current_stream())
     batch = spmv.Batch(plans, 4, [spmv.SPMV_BATCH_SORTED] * len(As))
     batch.set_io(Bs, Cs)
@@ -747,19 +752,16 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         "wall_s_timed": round(r["wall_s"], 4),
     }
     if not args.no_e2e:
-        # end to end through the C ABI: every step copies all members' B in from pinned host memory,
-        # runs the batched launch, and copies all C back
-        Bpin = [torch.from_numpy(B).pin_memory() for B in Bhs]
-        Cpin = [torch.empty((A.n_rows, 4), dtype=torch.float64).pin_memory() for A in As]
+        # end to end through the C ABI (spmv_batch_apply_host): every step copies all members' B in
+        # from pinned host memory, runs the batched launch, and copies all C back
+        Bpin_flat = torch.from_numpy(np.concatenate([B.ravel() for B in Bhs])).pin_memory()
+        Cpin_flat = torch.empty(sum(nc), dtype=torch.float64).pin_memory()
+        Bpin = list(torch.split(Bpin_flat, nb))
+        Cpin = list(torch.split(Cpin_flat, nc))
         n_e2e = 5
 
         def step():
-            with torch.cuda.stream(stream):
-                for Bd, Bp in zip(Bs, Bpin):
-                    Bd.copy_(Bp, non_blocking=True)
-                batch.apply(stream)
-                for Cd, Cp in zip(Cs, Cpin):
-                    Cp.copy_(Cd, non_blocking=True)
+            batch.apply_host(Bpin, Cpin, stream)
             stream.synchronize()
         step()
         timer.barrier()
@@ -769,7 +771,9 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         e2e_t = (time.perf_counter() - t0) / n_e2e
         line["e2e"] = {"value": round(flops * world / e2e_t / 1e9, 3), "unit": "GFlop/s",
                        "h2d_bytes_per_step": sum(8 * B.size for B in Bhs),
-                       "d2h_bytes_per_step": sum(32 * A.n_rows for A in As)}
+                       "d2h_bytes_per_step": sum(32 * A.n_rows for A in As),
+                       "api": "spmv_batch_apply_host (members back to back: one copy per operand), "
+                              "synchronised every step"}
     if not args.no_forms:
         forms = {}
         def med(fn, steps=20):

@@ -279,6 +279,16 @@ spmv_status spmv_batch_set_io(spmv_batch_handle b, const double* const* B_ptrs, 
  * reset + persistent kernel).  Asynchronous. */
 spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream);
 
+/* End to end from HOST buffers: each member's B_host[m] (n_cols_m x k, ld = k;
+ * pinned memory for asynchronous copies) is copied into the device B set by
+ * spmv_batch_set_io (overwriting it), the batch runs, and each member's C
+ * (n_rows_m x k) is copied back to C_host[m] (ld = k); one cudaMemcpyAsync
+ * per member and direction, all on `stream`.  Needs set_io with ldb = ldc = k
+ * (else SPMV_ERR_ARG).  Asynchronous: synchronise `stream` before reading
+ * C_host.  Host arrays B_host[count], C_host[count] are read during the call. */
+spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
+                                  void* stream);
+
 /* Same work as separate launches: one kernel per member, in member order (the
  * baseline the batched launch replaces).  Asynchronous. */
 spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream);

@@ -26,6 +26,7 @@ _SIGS = {
     "spmv_batch_create": ([_P(_vp), _i32, _vp, _i32, _vp, _P(spmv_batch_config)], ctypes.c_int),
     "spmv_batch_set_io": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_batch_apply": ([_vp, _vp], ctypes.c_int),
+    "spmv_batch_apply_host": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_batch_apply_separate": ([_vp, _vp], ctypes.c_int),
     "spmv_batch_set_config": ([_vp, _P(spmv_batch_config)], ctypes.c_int),
     "spmv_batch_get_config": ([_vp, _P(spmv_batch_config)], ctypes.c_int),
@@ -115,6 +116,17 @@ def spmv_batch_destroy(b) -> None:
     _check(_lib().spmv_batch_destroy(b))
 
 
+def _host_ptr(a) -> int:
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+def spmv_batch_apply_host(b, B_host_ptrs, C_host_ptrs, stream) -> None:
+    n = len(B_host_ptrs)
+    bp = (ctypes.c_void_p * n)(*B_host_ptrs)
+    cp = (ctypes.c_void_p * n)(*C_host_ptrs)
+    _check(_lib().spmv_batch_apply_host(b, bp, cp, stream))
+
+
 class Batch:
     """Owns one spmv_batch_handle over existing Plans (which must outlive it)."""
 
@@ -132,6 +144,13 @@ class Batch:
     def apply(self, stream=None) -> None:
         from . import _stream_handle
         spmv_batch_apply(self.handle, _stream_handle(stream))
+
+    def apply_host(self, B_host, C_host, stream=None) -> None:
+        """spmv_batch_apply_host: B_host[m] / C_host[m] are host float64 arrays or
+        (pinned) CPU tensors of each member's block (ld = k); asynchronous."""
+        from . import _stream_handle
+        spmv_batch_apply_host(self.handle, [_host_ptr(b) for b in B_host], [_host_ptr(c) for c in C_host],
+                              _stream_handle(stream))
 
     def apply_separate(self, stream=None) -> None:
         from . import _stream_handle

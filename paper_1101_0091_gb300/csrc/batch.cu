@@ -421,6 +421,53 @@ spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream) {
   return SPMV_OK;
 }
 
+spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
+                                  void* stream) {
+  if (!b || !B_host || !C_host) return fail(SPMV_ERR_ARG, "NULL argument");
+  if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
+  const size_t n = b->plans.size();
+  std::vector<int64_t> n_cols(n);
+  for (size_t m = 0; m < n; ++m) {
+    const BatchMat& M = b->h_mats[m];
+    if (M.ldb != b->k || M.ldc != b->k) return fail(SPMV_ERR_ARG, "the host path needs set_io with ldb = ldc = k");
+    spmv_info info;
+    spmv_status st = spmv_get_info(b->plans[m], &info);
+    if (st != SPMV_OK) return st;
+    n_cols[m] = info.n_cols;
+    if ((n_cols[m] > 0 && !B_host[m]) || (M.n_rows > 0 && !C_host[m])) return fail(SPMV_ERR_ARG, "NULL host buffer");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // members whose blocks follow one another both on the host and on the device
+  // (one allocation cut into views) move in one copy: a copy per member costs
+  // its own setup, which dominates for many small members
+  auto copy_runs = [&](auto dst_of, auto src_of, auto len_of, cudaMemcpyKind kind) -> cudaError_t {
+    size_t m = 0;
+    while (m < n) {
+      if (len_of(m) == 0) {
+        ++m;
+        continue;
+      }
+      char* dst = (char*)dst_of(m);
+      const char* src = (const char*)src_of(m);
+      size_t bytes = len_of(m);
+      size_t e = m + 1;
+      while (e < n && len_of(e) > 0 && (char*)dst_of(e) == dst + bytes && (const char*)src_of(e) == src + bytes)
+        bytes += len_of(e++);
+      cudaError_t err = cudaMemcpyAsync(dst, src, bytes, kind, s);
+      if (err != cudaSuccess) return err;
+      m = e;
+    }
+    return cudaSuccess;
+  };
+  const size_t kb = sizeof(double) * (size_t)b->k;
+  SPMV_CUDA(copy_runs([&](size_t m) { return (void*)b->h_mats[m].B; }, [&](size_t m) { return (const void*)B_host[m]; },
+                      [&](size_t m) { return kb * (size_t)n_cols[m]; }, cudaMemcpyHostToDevice));
+  SPMV_CUDA(cudaGraphLaunch(b->exec, s));
+  SPMV_CUDA(copy_runs([&](size_t m) { return (void*)C_host[m]; }, [&](size_t m) { return (const void*)b->h_mats[m].C; },
+                      [&](size_t m) { return kb * (size_t)b->h_mats[m].n_rows; }, cudaMemcpyDeviceToHost));
+  return SPMV_OK;
+}
+
 spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream) {
   if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
   if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");

@@ -117,6 +117,53 @@ def test_batch_separate_launches(lib):
     check(As, Bs, run_batch(lib, As, Bs, separate=True))
 
 
+def test_batch_host_path(lib):
+    """spmv_batch_apply_host: B from pinned host buffers into the batch's device
+    B, the batched launch, C back to host buffers; the same bits as the device
+    path, repeated steps with new inputs, and the refusal of padded blocks."""
+    import torch
+    As = members(12, seed=3)
+    plans = [lib.Plan.from_csr(A) for A in As]
+    Bd = [torch.zeros((A.n_cols, K), dtype=torch.float64, device="cuda") for A in As]
+    Cd = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+    stream = torch.cuda.Stream()
+    with lib.Batch(plans, K) as b:
+        b.set_io(Bd, Cd)
+        for step in range(3):
+            Bs = operands(As, seed=10 + step)
+            Bpin = [torch.from_numpy(B).pin_memory() for B in Bs]
+            Cpin = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64).pin_memory() for A in As]
+            b.apply_host(Bpin, Cpin, stream)
+            stream.synchronize()
+            Ch = [C.numpy().copy() for C in Cpin]
+            check(As, Bs, Ch)
+            b.apply(stream)                      # device path on the B the host path left behind
+            stream.synchronize()
+            for Cdev, C in zip(Cd, Ch):
+                assert np.array_equal(host(Cdev), C)
+        # members back to back in one device and one pinned allocation: one copy per operand, same bits
+        nb, nc = [A.n_cols * K for A in As], [A.n_rows * K for A in As]
+        Bf = torch.zeros(sum(nb), dtype=torch.float64, device="cuda")
+        Cf = torch.full((sum(nc),), float("nan"), dtype=torch.float64, device="cuda")
+        b.set_io([v.view(A.n_cols, K) for v, A in zip(torch.split(Bf, nb), As)],
+                 [v.view(A.n_rows, K) for v, A in zip(torch.split(Cf, nc), As)])
+        Bh = torch.from_numpy(np.concatenate([B.ravel() for B in Bs])).pin_memory()
+        Chf = torch.full((sum(nc),), float("nan"), dtype=torch.float64).pin_memory()
+        b.apply_host(list(torch.split(Bh, nb)), list(torch.split(Chf, nc)), stream)
+        stream.synchronize()
+        for C, Cp in zip(Ch, torch.split(Chf, nc)):
+            assert np.array_equal(Cp.numpy().reshape(C.shape), C)
+        b.set_io(Bd, Cd)
+        # a padded block (ld > k) cannot take the host path
+        Bw = [torch.zeros((A.n_cols, K + 2), dtype=torch.float64, device="cuda") for A in As]
+        b.set_io(Bw, Cd)
+        with pytest.raises(lib.SpmvError) as e:
+            b.apply_host(Bpin, Cpin, stream)
+        assert e.value.status == 1
+    for p in plans:
+        p.close()
+
+
 def test_batch_replay_autotune_and_new_io(lib):
     import torch
     As = members(16)
