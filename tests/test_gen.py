@@ -89,3 +89,29 @@ def test_uniform_rhs():
     assert v.min() >= -1.0 and v.max() < 1.0 and abs(v.mean()) < 0.01
     assert np.array_equal(v, gen.uniform(100000, seed=0))
     assert not np.array_equal(v[:100], gen.uniform(100, seed=1))
+
+
+def test_kronecker_transpose_is_the_index_map():
+    """Sec. 1.3.1: the two numberings of the n1 x n2 product basis differ in
+    which factor is contiguous.  The renumbering takes old index e*n2 + p to
+    new index p*n1 + e, so perm[new] = old is perm[p*n1 + e] = e*n2 + p.
+    Pinned by a hand-worked 2 x 3 case, by the map written out with loops,
+    and by the inverse map decoded from the new index (q = p*n1 + e)."""
+    # 2 x 3: old (e, p) -> new p*2 + e: (0,0)->0 (1,0)->1 (0,1)->2 (1,1)->3 (0,2)->4 (1,2)->5
+    assert gen.kronecker_transpose(2, 3).tolist() == [0, 3, 1, 4, 2, 5]
+    for n1, n2 in ((3, 5), (400, 7), (7, 400)):
+        perm = gen.kronecker_transpose(n1, n2)
+        ref = np.empty(n1 * n2, np.int64)
+        for e in range(n1):
+            for p in range(n2):
+                ref[p * n1 + e] = e * n2 + p
+        assert np.array_equal(perm, ref)
+        assert np.array_equal(np.sort(perm), np.arange(n1 * n2))      # a permutation
+    n1, n2 = 400, 15_504                                             # the full eigenproblem basis
+    perm = gen.kronecker_transpose(n1, n2)
+    q = np.arange(n1 * n2, dtype=np.int64)
+    assert perm.dtype == np.int32 and np.array_equal(perm, (q % n1) * n2 + q // n1)
+    inv = np.empty_like(q)
+    inv[perm] = q
+    old = np.arange(n1 * n2, dtype=np.int64)
+    assert np.array_equal(inv, (old % n2) * n1 + old // n2)          # old e*n2 + p sits at p*n1 + e

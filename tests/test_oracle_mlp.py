@@ -78,3 +78,24 @@ def test_adam_first_step_is_lr_times_sign():
     v_hat = 0.999 * 0.001 * np.array([0.09, 4.0]) / (1 - 0.999 ** 2)
     for k in mlp.PARAM_NAMES:
         assert np.allclose(p[k] - before[k], -0.01 * m_hat / (np.sqrt(v_hat) + 1e-8), rtol=1e-12)
+
+
+def test_adam_steps_two_and_three_hand_computed():
+    """Adam (Kingma and Ba) on one parameter, worked by hand in exact fractions
+    with beta1 = 1/2, beta2 = 3/4, lr = 1/10, eps = 0 and gradients 2, -2, 2:
+
+      t=1: m = 1,    v = 1,     m^ = 1/(1/2) = 2,       v^ = 1/(1/4) = 4,        p = 0 - (1/10)(2/2)       = -1/10
+      t=2: m = -1/2, v = 7/4,   m^ = (-1/2)/(3/4) = -2/3, v^ = (7/4)/(7/16) = 4,  p = -1/10 + (1/10)(1/3)  = -1/15
+      t=3: m = 3/4,  v = 37/16, m^ = (3/4)/(7/8) = 6/7,   v^ = (37/16)/(37/64) = 4, p = -1/15 - (1/10)(3/7) = -23/210
+
+    A first moment or second moment not carried from one step to the next, or
+    a bias correction with the wrong power of beta, changes steps 2 and 3."""
+    p = {k: np.zeros(1) for k in mlp.PARAM_NAMES}
+    st = {}
+    expected = [-1 / 10, -1 / 15, -23 / 210]
+    for t, (gv, want) in enumerate(zip((2.0, -2.0, 2.0), expected), start=1):
+        g = {k: np.array([gv]) for k in mlp.PARAM_NAMES}
+        mlp.adam_step(p, g, st, t, lr=0.1, beta1=0.5, beta2=0.75, eps=0.0)
+        for k in mlp.PARAM_NAMES:
+            assert p[k][0] == pytest.approx(want, rel=1e-15, abs=1e-17), (t, k)
+    assert st["m_W1"][0] == pytest.approx(0.75, rel=1e-15) and st["v_W1"][0] == pytest.approx(37 / 16, rel=1e-15)
