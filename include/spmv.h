@@ -81,9 +81,12 @@ typedef struct {
   int32_t sell_sigma;   /* sigma of SPMV_SELL (sorting window); <= 1 means no sorting           */
   int32_t val_fp32;     /* 1: store val as float32 (exactly widened to FP64 before each FMA)    */
   int32_t max_k;        /* largest k for spmv_apply_block (1..16); 0 means 16                   */
-  int64_t halo_begin;   /* >= 0: build the local/halo column split at column h (Sec. 3.1);     */
-                        /* -1: no split.  A zero-initialised struct is NOT the default: use     */
-                        /* spmv_default_options().                                               */
+  int32_t split;        /* 1: build the local/halo column split at column halo_begin (Sec. 3.1); */
+                        /* 0: no split                                                           */
+  int32_t reserved;     /* must be 0                                                             */
+  int64_t halo_begin;   /* h of the split, 0 <= h <= n_cols (read only when split = 1)          */
+                        /* A zero-initialised struct is the default (AUTO, no sorting, FP64     */
+                        /* values, max_k 16, no split), the same as spmv_default_options().     */
 } spmv_options;
 
 typedef struct {
@@ -101,7 +104,8 @@ typedef struct {
   int64_t sym_nnz;          /* stored entries of the SPMV_SYM triangle (0 if not built)         */
 } spmv_info;
 
-/* Default options: AUTO, sigma 1, FP64 values, max_k 16, no split. */
+/* Default options: AUTO, sigma 1, FP64 values, max_k 16, no split (a zero-initialised
+ * spmv_options means the same). */
 spmv_options spmv_default_options(void);
 
 /* Thread-local text of the last error ("" if none). */
@@ -109,10 +113,12 @@ const char* spmv_last_error(void);
 
 /* Create a plan on the current CUDA device from HOST CRS arrays (copied;
  * the caller keeps them).  row_ptr has n_rows+1 entries with row_ptr[0] = 0,
- * non-decreasing, row_ptr[n_rows] = nnz <= 2^31-1; 0 <= col_idx < n_cols.
+ * non-decreasing, row_ptr[n_rows] = nnz <= 2^31-1; col_idx and val have nnz
+ * entries with 0 <= col_idx < n_cols.  nnz is the caller's count of stored
+ * entries; it must equal row_ptr[n_rows] (a mismatch is SPMV_ERR_CSR).
  * Violations return SPMV_ERR_CSR before anything is allocated on the device.
  * Sec. 1.2 (CRS format).  opt may be NULL (defaults). */
-spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols,
+spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
                         const int32_t* row_ptr, const int32_t* col_idx, const double* val,
                         const spmv_options* opt);
 
@@ -135,7 +141,7 @@ spmv_status spmv_apply_block(spmv_handle h, const double* B_dev, int32_t k, int6
  * CRS variant, CRS_L1 for SELL and SYM plans) writes C on main_stream;
  * main_stream then waits for the copy and the halo kernel adds
  * the entries with col >= h into C.  B_dev[0:h] must already hold the local
- * part.  Requires a plan built with halo_begin = h.  copy_stream may equal
+ * part.  Requires a plan built with split = 1, halo_begin = h.  copy_stream may equal
  * main_stream (no overlap).  On return all work is enqueued; main_stream
  * carries the completion of both. */
 spmv_status spmv_apply_split(spmv_handle h, double* B_dev, const double* B_halo_pinned,
@@ -270,8 +276,12 @@ spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_
 
 /* Set the members' operands: B_ptrs[m] (n_cols_m x ldb[m]) and C_ptrs[m]
  * (n_rows_m x ldc[m]) are DEVICE pointers held in host arrays; ldb/ldc NULL
- * means k.  Copied to the device member table (synchronously); call again to
- * move the batch to other buffers. */
+ * means k.  B_ptrs[m] may be NULL only for a member without nonzeros, C_ptrs[m]
+ * only for a member without rows (else SPMV_ERR_ARG).  The call first waits
+ * until the batch's last enqueued replay (spmv_batch_apply or
+ * spmv_batch_apply_host, on whatever stream) has finished, then copies the
+ * pointers into the device member table; call again to move the batch to other
+ * buffers.  Replays enqueued after it read the new operands. */
 spmv_status spmv_batch_set_io(spmv_batch_handle b, const double* const* B_ptrs, const int64_t* ldb,
                               double* const* C_ptrs, const int64_t* ldc);
 
@@ -283,7 +293,9 @@ spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream);
  * pinned memory for asynchronous copies) is copied into the device B set by
  * spmv_batch_set_io (overwriting it), the batch runs, and each member's C
  * (n_rows_m x k) is copied back to C_host[m] (ld = k); one cudaMemcpyAsync
- * per member and direction, all on `stream`.  Needs set_io with ldb = ldc = k
+ * per direction and run of consecutive members whose blocks follow one another
+ * both on the host and on the device (one copy per member when they do not),
+ * all on `stream`.  Needs set_io with ldb = ldc = k
  * (else SPMV_ERR_ARG).  Asynchronous: synchronise `stream` before reading
  * C_host.  Host arrays B_host[count], C_host[count] are read during the call. */
 spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
@@ -502,6 +514,31 @@ spmv_status spmv_reorder_gather(spmv_reorder_handle h, int32_t k, const double* 
 spmv_status spmv_reorder_scatter(spmv_reorder_handle h, int32_t k, const double* X_dev, int64_t ldx, double* Y_dev,
                                  int64_t ldy, void* stream);
 spmv_status spmv_reorder_destroy(spmv_reorder_handle h);
+
+/* ----------------------------------------------------------------------------
+ * Measurement probes: the machine side of the balance model.  Sec. 2 sets the
+ * code balance of Eq. 1 against the machine's measured memory bandwidth
+ * (STREAM); on this GPU two more rates bound forms of the product, and these
+ * probes measure them with kernels of their own (CUDA events on a private
+ * stream, best of `reps` launches after one untimed launch; synchronous on the
+ * current device; each allocates and frees its own device buffers).
+ * ------------------------------------------------------------------------- */
+
+/* FP64 fused multiply-add rate: every thread of a grid filling all SMs runs 8
+ * independent FMA chains.  *gflops = 2 x FMAs / time (1e9 flop/s); *ms the
+ * best launch time; *sm_count the device's multiprocessors (any output may be
+ * NULL).  Bounds the products with k >= 2 columns, where each stored entry
+ * needs k FMAs (and the batch, the solvers). */
+spmv_status spmv_probe_fp64(int32_t reps, double* gflops, double* ms, int32_t* sm_count);
+
+/* Random 8-byte read rate: a grid filling all SMs reads uniformly random
+ * entries of a zero-filled buffer of n_elems doubles (1 <= n_elems <=
+ * 2^31-1) with read-only loads, 8 independent reads in flight per thread.
+ * *gathers_per_s = reads / time; *ms the best launch time.  A buffer the size
+ * of B of the eigenproblem-shaped workload (6,201,600 doubles, 50 MB) stays in
+ * L2: the rate bounds a product whose B gathers are scattered (each read moves
+ * a whole 32-byte sector for 8 useful bytes). */
+spmv_status spmv_probe_gather(int64_t n_elems, int32_t reps, double* gathers_per_s, double* ms);
 
 /* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).

@@ -15,6 +15,7 @@ import numpy as np
 
 from . import _binding as _b
 from ._binding import spmv_apply_host_async, spmv_host_sync, spmv_selftest_wait_timeout, spmv_wait  # noqa: F401
+from ._binding import spmv_probe_fp64, spmv_probe_gather  # noqa: F401
 from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_block, spmv_apply_host,  # noqa: F401
                        spmv_apply_split, spmv_check, spmv_create, spmv_default_options, spmv_destroy,
                        spmv_get_info, spmv_last_error, spmv_options, spmv_sell_export, spmv_set_variant,
@@ -126,14 +127,18 @@ class Plan:
     """Owns one spmv_handle.  Host CRS arrays are copied at construction."""
 
     def __init__(self, n_rows: int, n_cols: int, row_ptr, col_idx, val, *, variant: int = SPMV_VARIANT_AUTO,
-                 sell_sigma: int = 1, val_fp32: bool = False, max_k: int = 16, halo_begin: int = -1):
+                 sell_sigma: int = 1, val_fp32: bool = False, max_k: int = 16, halo_begin: int | None = None):
         rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
         ci = np.ascontiguousarray(col_idx, dtype=np.int32)
         va = np.ascontiguousarray(val, dtype=np.float64)
         o = spmv_default_options()
-        o.variant, o.sell_sigma, o.val_fp32, o.max_k, o.halo_begin = variant, sell_sigma, int(val_fp32), max_k, halo_begin
+        o.variant, o.sell_sigma, o.val_fp32, o.max_k = variant, sell_sigma, int(val_fp32), max_k
+        if halo_begin is not None:   # local/halo split at column halo_begin
+            o.split, o.halo_begin = 1, halo_begin
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
-        self.handle = spmv_create(n_rows, n_cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, o)
+        # nnz is the count of stored entries the caller hands over; the library
+        # checks it against row_ptr[n_rows]
+        self.handle = spmv_create(n_rows, n_cols, len(ci), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, o)
 
     @classmethod
     def from_csr(cls, A, **kw) -> "Plan":

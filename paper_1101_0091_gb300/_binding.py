@@ -38,7 +38,8 @@ class SpmvError(RuntimeError):
 
 class spmv_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("sell_sigma", ctypes.c_int32), ("val_fp32", ctypes.c_int32),
-                ("max_k", ctypes.c_int32), ("halo_begin", ctypes.c_int64)]
+                ("max_k", ctypes.c_int32), ("split", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("halo_begin", ctypes.c_int64)]
 
 
 class spmv_info(ctypes.Structure):
@@ -53,7 +54,8 @@ _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 _SIGS = {
     "spmv_default_options": ([], spmv_options),
     "spmv_last_error": ([], ctypes.c_char_p),
-    "spmv_create": ([ctypes.POINTER(_vp), _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(spmv_options)], ctypes.c_int),
+    "spmv_create": ([ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(spmv_options)],
+                    ctypes.c_int),
     "spmv_destroy": ([_vp], ctypes.c_int),
     "spmv_apply": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_apply_block": ([_vp, _vp, _i32, _i64, _vp, _i64, _vp], ctypes.c_int),
@@ -72,6 +74,8 @@ _SIGS = {
     "spmv_split_build_host": ([_i64, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
     "spmv_sym_build_host": ([_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_probe_fp64": ([_i32, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_probe_gather": ([_i64, _i32, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -110,9 +114,10 @@ def spmv_last_error() -> str:
     return load().spmv_last_error().decode()
 
 
-def spmv_create(n_rows: int, n_cols: int, row_ptr: int, col_idx: int, val: int, opt: spmv_options | None = None):
+def spmv_create(n_rows: int, n_cols: int, nnz: int, row_ptr: int, col_idx: int, val: int,
+                opt: spmv_options | None = None):
     h = ctypes.c_void_p()
-    _check(load().spmv_create(ctypes.byref(h), n_rows, n_cols, row_ptr, col_idx, val,
+    _check(load().spmv_create(ctypes.byref(h), n_rows, n_cols, nnz, row_ptr, col_idx, val,
                               ctypes.byref(opt) if opt is not None else None))
     return h
 
@@ -225,3 +230,17 @@ def spmv_wait(stream: int, timeout_ms: int) -> None:
 
 def spmv_selftest_wait_timeout(limit_us: int) -> None:
     _check(load().spmv_selftest_wait_timeout(limit_us))
+
+
+def spmv_probe_fp64(reps: int = 5) -> dict:
+    """FP64 FMA rate of the current device (spmv_probe_fp64)."""
+    g, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(load().spmv_probe_fp64(reps, ctypes.byref(g), ctypes.byref(ms), ctypes.byref(sms)))
+    return {"gflops": g.value, "ms": ms.value, "sm_count": sms.value}
+
+
+def spmv_probe_gather(n_elems: int, reps: int = 5) -> dict:
+    """Random 8-byte read rate out of a buffer of n_elems doubles (spmv_probe_gather)."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().spmv_probe_gather(n_elems, reps, ctypes.byref(r), ctypes.byref(ms)))
+    return {"gathers_per_s": r.value, "ms": ms.value}

@@ -334,24 +334,31 @@ spmv_options spmv_default_options(void) {
   o.sell_sigma = 1;
   o.val_fp32 = 0;
   o.max_k = 16;
-  o.halo_begin = -1;
+  o.split = 0;
+  o.halo_begin = 0;
   return o;
 }
 
 const char* spmv_last_error(void) { return g_last_error.c_str(); }
 
-spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, const int32_t* row_ptr,
+spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr,
                         const int32_t* col_idx, const double* val, const spmv_options* opt) {
   if (!out) return fail(SPMV_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (nnz < 0 || nnz > INT32_MAX) return fail(SPMV_ERR_CSR, "nnz outside [0, 2^31-1]");
   std::string why;
   if (!validate_csr(n_rows, n_cols, row_ptr, col_idx, &why)) return fail(SPMV_ERR_CSR, why);
-  const int64_t nnz = row_ptr[n_rows];
+  if (row_ptr[n_rows] != nnz)
+    return fail(SPMV_ERR_CSR, "row_ptr[n_rows] = " + std::to_string(row_ptr[n_rows]) + " differs from nnz = " +
+                                  std::to_string(nnz));
   if (nnz > 0 && !val) return fail(SPMV_ERR_ARG, "val is NULL");
   spmv_options o = opt ? *opt : spmv_default_options();
   if (o.max_k == 0) o.max_k = 16;
+  if (o.sell_sigma < 1) o.sell_sigma = 1;
   if (o.max_k < 1 || o.max_k > 16) return fail(SPMV_ERR_ARG, "max_k must be in 1..16");
-  if (o.halo_begin > n_cols) return fail(SPMV_ERR_ARG, "halo_begin > n_cols");
+  if (o.split != 0 && o.split != 1) return fail(SPMV_ERR_ARG, "split must be 0 or 1");
+  if (o.reserved != 0) return fail(SPMV_ERR_ARG, "reserved option field must be 0");
+  if (o.split && (o.halo_begin < 0 || o.halo_begin > n_cols)) return fail(SPMV_ERR_ARG, "halo_begin outside [0, n_cols]");
   std::unique_ptr<spmv_plan> p;
   try {
     p.reset(new spmv_plan());
@@ -381,7 +388,7 @@ spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, const 
   e = upload(p->arena, &status, (const int*)nullptr, 0, 4);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "status word"));
   p->status = status;
-  if (o.halo_begin >= 0) {
+  if (o.split) {
     st = build_split_dev(p.get(), o.halo_begin);
     if (st != SPMV_OK) return cleanup(st);
   }
@@ -490,7 +497,7 @@ spmv_status spmv_apply(spmv_handle h, const double* B_dev, double* C_dev, void* 
 spmv_status spmv_apply_split(spmv_handle h, double* B_dev, const double* B_halo_pinned, double* C_dev,
                              void* main_stream, void* copy_stream) {
   if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
-  if (!h->has_split) return fail(SPMV_ERR_UNSUPPORTED, "plan was built without halo_begin");
+  if (!h->has_split) return fail(SPMV_ERR_UNSUPPORTED, "plan was built without a split (options.split = 0)");
   if (h->host.n_rows == 0) return SPMV_OK;
   const int64_t hb = h->split_host.h, nhalo = h->host.n_cols - hb;
   if (!C_dev || !B_dev || (nhalo > 0 && !B_halo_pinned)) return fail(SPMV_ERR_ARG, "NULL buffer");
@@ -706,7 +713,7 @@ spmv_status spmv_sym_export(spmv_handle h, int32_t* row_ptr, int32_t* col, doubl
 spmv_status spmv_split_export(spmv_handle h, int32_t* loc_row_ptr, int32_t* loc_col, double* loc_val,
                               int32_t* halo_rows, int32_t* halo_row_ptr, int32_t* halo_col, double* halo_val) {
   if (!h) return fail(SPMV_ERR_ARG, "handle is NULL");
-  if (!h->has_split) return fail(SPMV_ERR_UNSUPPORTED, "plan was built without halo_begin");
+  if (!h->has_split) return fail(SPMV_ERR_UNSUPPORTED, "plan was built without a split (options.split = 0)");
   DeviceGuard g(h->device);
   const CsrDev& L = h->local;
   const HaloDev& H = h->halo;

@@ -201,6 +201,9 @@ struct spmv_batch_plan {
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // recorded on the caller's stream after every replay: set_io waits on it
+  // before it rewrites the member table a replay in flight may still read
+  cudaEvent_t ev_last = nullptr;
   bool io_set = false;
   bool vec = false;  // 16-byte loads/stores of right-hand-side rows
   // length-sorted SELL copy of the sorted-policy members (rebuilt when the policies change)
@@ -378,6 +381,7 @@ spmv_status spmv_batch_create(spmv_batch_handle* out, int32_t count, const spmv_
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_last, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(cuda_fail(e, "batch allocation"));
   st = rebuild(b);
   if (st != SPMV_OK) return bail(st);
@@ -393,7 +397,11 @@ spmv_status spmv_batch_set_io(spmv_batch_handle b, const double* const* B_ptrs, 
     const int64_t lb = ldb ? ldb[m] : b->k, lc = ldc ? ldc[m] : b->k;
     if (lb < b->k || lc < b->k) return fail(SPMV_ERR_ARG, "ldb/ldc must be >= k");
     if (!C_ptrs[m] && b->h_mats[m].n_rows > 0) return fail(SPMV_ERR_ARG, "NULL C pointer");
+    if (!B_ptrs[m] && plan_csr(b->plans[m])->nnz > 0)
+      return fail(SPMV_ERR_ARG, "NULL B pointer of member " + std::to_string(m) + " (it has nonzeros)");
   }
+  // a replay enqueued earlier (on any stream) may still read the table: wait for it
+  SPMV_CUDA(cudaEventSynchronize(b->ev_last));
   bool vec = (b->k % 2 == 0);
   for (size_t m = 0; m < b->h_mats.size(); ++m) {
     const int64_t lb = ldb ? ldb[m] : b->k, lc = ldc ? ldc[m] : b->k;
@@ -418,6 +426,7 @@ spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream) {
   if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
   if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
   SPMV_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  SPMV_CUDA(cudaEventRecord(b->ev_last, (cudaStream_t)stream));
   return SPMV_OK;
 }
 
@@ -463,6 +472,7 @@ spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_ho
   SPMV_CUDA(copy_runs([&](size_t m) { return (void*)b->h_mats[m].B; }, [&](size_t m) { return (const void*)B_host[m]; },
                       [&](size_t m) { return kb * (size_t)n_cols[m]; }, cudaMemcpyHostToDevice));
   SPMV_CUDA(cudaGraphLaunch(b->exec, s));
+  SPMV_CUDA(cudaEventRecord(b->ev_last, s));
   SPMV_CUDA(copy_runs([&](size_t m) { return (void*)C_host[m]; }, [&](size_t m) { return (const void*)b->h_mats[m].C; },
                       [&](size_t m) { return kb * (size_t)b->h_mats[m].n_rows; }, cudaMemcpyDeviceToHost));
   return SPMV_OK;
@@ -577,6 +587,7 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b) {
   if (!b) return SPMV_OK;
   cudaDeviceSynchronize();
   free_graph(b);
+  if (b->ev_last) cudaEventDestroy(b->ev_last);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_rowlist) cudaFree(b->d_rowlist);

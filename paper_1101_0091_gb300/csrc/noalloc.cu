@@ -65,10 +65,7 @@ extern "C" spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_
     return fail(SPMV_ERR_ARG, "spmv_batch_apply_noalloc: more than 8192 members (scratch limit)");
   if (k < 1 || k > 16) return fail(SPMV_ERR_ARG, "k out of range 1..16");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  void* scratch = nullptr;
-  spmv_status st = noalloc_scratch(&scratch);
-  if (st != SPMV_OK) return st;
-
+  // every argument is checked and the work list built before the first CUDA call
   BatchMat* table = reinterpret_cast<BatchMat*>(g_noalloc_host + kNoAllocCounterBytes);
   BatchItem* items = reinterpret_cast<BatchItem*>(g_noalloc_host + kNoAllocItemsOffset);
   size_t n_items = 0;
@@ -80,7 +77,8 @@ extern "C" spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_
     const int64_t lb = ldb ? ldb[m] : k, lc = ldc ? ldc[m] : k;
     if (n_rows[m] < 0 || n_rows[m] > INT32_MAX) return fail(SPMV_ERR_ARG, "n_rows out of range");
     if (lb < k || lc < k) return fail(SPMV_ERR_ARG, "ldb/ldc must be >= k");
-    if (n_rows[m] > 0 && (!row_ptr_dev[m] || !C_dev[m])) return fail(SPMV_ERR_ARG, "NULL row_ptr or C");
+    if (n_rows[m] > 0 && (!row_ptr_dev[m] || !col_dev[m] || !val_dev[m] || !B_dev[m] || !C_dev[m]))
+      return fail(SPMV_ERR_ARG, "NULL row_ptr, col, val, B or C of member " + std::to_string(m) + " (it has rows)");
     table[m] = BatchMat{row_ptr_dev[m], col_dev[m], val_dev[m], B_dev[m], C_dev[m], lb, lc, n_rows[m]};
     vec = vec && lb % 2 == 0 && lc % 2 == 0 && (uintptr_t)B_dev[m] % 16 == 0 && (uintptr_t)C_dev[m] % 16 == 0;
     const int64_t per = (int64_t)(32 / L) * kNoAllocPasses;
@@ -91,6 +89,9 @@ extern "C" spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_
       items[n_items++] = BatchItem{m, (int32_t)r0, (int32_t)r1, 0, (int16_t)L, 0, 0};
     }
   }
+  void* scratch = nullptr;
+  spmv_status st = noalloc_scratch(&scratch);
+  if (st != SPMV_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* d = static_cast<unsigned char*>(scratch);
   // the counter starts at zero on every call; the table and items overwrite the last call's

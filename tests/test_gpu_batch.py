@@ -220,3 +220,36 @@ def test_batch_empty_members_and_errors(lib):
             with pytest.raises(lib.SpmvError):
                 b.set_io([dev(np.zeros((A.n_cols, 4)))], [torch.zeros((A.n_rows, 2), dtype=torch.float64,
                                                                         device="cuda")])
+
+
+def test_set_io_waits_for_a_replay_on_a_non_blocking_stream(lib):
+    """spmv_batch_set_io rewrites the device member table that a replay reads.
+    A replay enqueued just before on a non-blocking stream (queued behind a
+    busy kernel, so it has not started when set_io runs) must still see the
+    operands it was enqueued with: set_io waits for it.  Both replays are
+    checked against the oracle."""
+    import torch
+    As = members(16, seed=5)
+    Bs1, Bs2 = operands(As, seed=21), operands(As, seed=22)
+    plans = [lib.Plan.from_csr(A) for A in As]
+    B1, B2 = [dev(B) for B in Bs1], [dev(B) for B in Bs2]
+    C1 = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+    C2 = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+    s = torch.cuda.Stream()                      # non-blocking with respect to the legacy stream
+    torch.cuda.synchronize()
+    with lib.Batch(plans, K) as b:
+        b.set_io(B1, C1)
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(100_000_000)       # a bounded spin (about 50 ms) ahead of the replay
+        b.apply(s)
+        b.set_io(B2, C2)                         # returns only once the replay above has run
+        b.apply(s)
+        s.synchronize()
+        check(As, Bs1, [host(C) for C in C1])
+        check(As, Bs2, [host(C) for C in C2])
+        # a member with nonzeros but no B is refused on the host
+        with pytest.raises(lib.SpmvError) as e:
+            lib.spmv_batch_set_io(b.handle, [0] * len(As), None, [C.data_ptr() for C in C1], None)
+        assert e.value.status == 1 and "NULL B" in str(e.value)
+    for p in plans:
+        p.close()

@@ -280,3 +280,28 @@ def test_pipelined_host_steps(lib, k):
         p.host_sync()
         for i in range(steps):
             assert_close(Cp[i].numpy(), A, Bs[steps - 1 - i])
+
+
+def test_zero_initialised_options_build_the_default_plan(lib):
+    """spmv_create with a zero-initialised spmv_options, with NULL options and
+    with spmv_default_options() builds the same plan (AUTO -> CRS_L1, FP64
+    values, no split) and the same product bit for bit; nnz is the caller's
+    count of stored entries."""
+    import torch
+    A = case("powerlaw")
+    B = dev(gen.uniform(A.n_cols, seed=3))
+    rp, ci, va = (np.ascontiguousarray(x) for x in (A.row_ptr, A.col_idx, A.val))
+    outs, infos = [], []
+    for opt in (lib.spmv_options(), None, lib.spmv_default_options()):
+        h = lib.spmv_create(A.n_rows, A.n_cols, A.nnz, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, opt)
+        try:
+            C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+            lib.spmv_apply(h, B.data_ptr(), C.data_ptr(), torch.cuda.current_stream().cuda_stream)
+            outs.append(host(C))
+            i = lib.spmv_get_info(h)
+            infos.append((i.variant, i.val_fp32, i.n_halo_rows, i.halo_nnz, i.sell_sigma))
+        finally:
+            lib.spmv_destroy(h)
+    assert infos[0] == infos[1] == infos[2] == (lib.SPMV_CRS_L1, 0, 0, 0, 0)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert_close(outs[0], A, gen.uniform(A.n_cols, seed=3))
