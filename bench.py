@@ -47,8 +47,17 @@ WORKLOADS = {
 VARIANTS = {"crs_staged": (1, 1), "crs_l1": (2, 1), "crs_l2": (3, 1), "crs_l4": (4, 1), "crs_l8": (5, 1),
             "crs_l16": (6, 1), "crs_l32": (7, 1), "sell_s1": (8, 1), "sell_s256": (8, 256), "sell_s4096": (8, 4096),
             "sym": (9, 1)}
-# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP64 rate from unit counts and the highest SM clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+# Context only: the roofs below use the rate the FP64 probe measures on the device in the same run.
+FP64_UNIT_COUNT_GFLOPS = 152 * 2 * 2 * 2.07
+MACHINE = {"fp64_gflops": FP64_UNIT_COUNT_GFLOPS, "fp64_kind": "unit count (probe not run)"}
+
+
+def fp64_peak() -> float:
+    """FP64 FMA rate (GFLOP/s) used as the ALU roof: the probe's measurement."""
+    return MACHINE["fp64_gflops"]
+
+
 # The paper's own single-socket CRS numbers (Sec. 2), quoted as context only: other hardware,
 # other (real) matrix; its multi-node results (QDR-InfiniBand Westmere cluster, Cray XE6) exist
 # only as figures.
@@ -58,6 +67,56 @@ PAPER_CONTEXT = {"hardware": "Intel Xeon X5550 (Nehalem EP), one socket, 4 cores
                  "kappa_bytes_per_nnz": 2.5, "hmep_kappa": 3.79,
                  "multi_node": "QDR-InfiniBand Westmere cluster and Cray XE6: figures only, no numbers",
                  "note": "context, not a target: no vs_baseline is computed from it"}
+
+
+def sm_max_mhz() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            v = json.load(f).get("sm_max_mhz")
+            if v:
+                return float(v)
+    return 2070.0
+
+
+def probe_machine(spmv) -> dict:
+    """Secondary roofs measured by the library's own probe kernels in this run.
+    Each probe also reads the SM clock it ran at (clock cycles over globaltimer
+    nanoseconds), so its rate per SM and clock is known; the roofs are that
+    rate at the highest SM clock (the clock the bench's kernels run at):
+      FP64: FMAs per SM and clock (spmv_probe_fp64);
+      requests: random 8-byte reads per SM and clock out of an L2-resident
+                buffer the size of the eigenproblem matrix's B
+                (spmv_probe_gather); each is one request from the SM's L1 to
+                the crossbar, the port that bounds scattered gathers.
+    The HBM copy peak comes from the driver's measurement."""
+    f = spmv.spmv_probe_fp64(5)
+    l2 = spmv.spmv_probe_gather(6_201_600, 5)
+    dram = spmv.spmv_probe_gather(1 << 28, 3)
+    hbm, kind = measured_hbm()
+    sms, fmax = f["sm_count"], sm_max_mhz()
+    fma_clk = f["gflops"] * 1e3 / (2 * sms * f["sm_mhz"])
+    req_clk = l2["gathers_per_s"] / (sms * l2["sm_mhz"] * 1e6)
+    MACHINE.update({"fp64_gflops": fma_clk * 2 * sms * fmax / 1e3,
+                    "fp64_kind": f"measured: {fma_clk:.3f} FMA per SM and clock (spmv_probe_fp64) x {sms} SMs "
+                                 f"x 2 flop x {fmax:.0f} MHz",
+                    "l2_gathers_per_s": req_clk * sms * fmax * 1e6,
+                    "dram_gathers_per_s": dram["gathers_per_s"]})
+    return {"sm_count": sms, "sm_max_mhz": fmax,
+            "fp64": {"probe_gflops": round(f["gflops"], 1), "probe_sm_mhz": round(f["sm_mhz"], 1),
+                     "fma_per_sm_per_clock": round(fma_clk, 4),
+                     "peak_gflops_at_max_clock": round(MACHINE["fp64_gflops"], 1),
+                     "unit_count_gflops": round(FP64_UNIT_COUNT_GFLOPS, 1)},
+            "random_reads_l2": {"probe_per_s": round(l2["gathers_per_s"] / 1e9, 2), "unit": "1e9 per s",
+                                "probe_sm_mhz": round(l2["sm_mhz"], 1),
+                                "per_sm_per_clock": round(req_clk, 4),
+                                "peak_at_max_clock": round(MACHINE["l2_gathers_per_s"] / 1e9, 2)},
+            "random_reads_hbm": {"probe_per_s": round(dram["gathers_per_s"] / 1e9, 2), "unit": "1e9 per s",
+                                 "buffer_bytes": 8 << 28},
+            "hbm_gbs": hbm, "hbm_kind": kind,
+            "how": "spmv_probe_fp64: 8 FMA chains per thread with register operands, all SMs; "
+                   "spmv_probe_gather: random 8-byte read-only loads, 8 in flight per thread, over 6,201,600 "
+                   "doubles (50 MB, L2-resident) and 2^28 doubles (2 GB); best of 5 / 3 launches"}
 
 
 def parse():
@@ -71,6 +130,12 @@ def parse():
     ap.add_argument("--fp32-val", action="store_true", help="store val in FP32 (FP64 accumulation)")
     ap.add_argument("--k", type=int, default=1, help="right-hand sides per product (single-matrix workloads)")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--configs", default="auto",
+                    help="extra configuration sections in the line: laplace, eigen, batch (comma list), all, none; "
+                         "auto = all for the default 280^3 headline, none otherwise")
+    ap.add_argument("--no-probes", action="store_true", help="skip the FP64 / random-read probes (unit-count roofs)")
+    ap.add_argument("--prefetch", type=int, default=None,
+                    help="L2 prefetch distance of the timed plan (default: the plan's own choice)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
@@ -328,6 +393,8 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     Bh = gen.uniform(A.n_cols, seed=0) if k == 1 else gen.rhs_block(A.n_cols, k, seed=0)
     vid, sigma = VARIANTS[args.variant]
     plan = spmv.Plan.from_csr(A, variant=vid, sell_sigma=sigma, val_fp32=args.fp32_val)
+    if args.prefetch is not None:
+        plan.set_tuning(prefetch_distance=args.prefetch)
     B = torch.from_numpy(Bh).cuda()
     C = torch.empty((A.n_rows,) if k == 1 else (A.n_rows, k), dtype=torch.float64, device="cuda")
     stream.wait_stream(torch.cuda.current_stream())
@@ -348,6 +415,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "kernel": args.variant,
+                   "prefetch_distance": plan.tuning().prefetch_distance,
                    "val_storage": "f32" if args.fp32_val else "f64", "k": k, "n_rows": A.n_rows, "nnz": A.nnz,
                    "l2": (f"inputs larger than L2 ({tr.bytes_min / 1e9:.2f} GB vs 129 MB), no flush"
                           if tr.bytes_min > 2 * 129e6 else "inputs L2-resident (warm figure)"),
@@ -358,7 +426,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
                           "traffic": ncu_traffic(kname, args.workload),
                           "algorithmic_bytes_per_launch": tr.bytes_min,
                           "frac_of_nominal_7900": round(achieved / 7900.0, 4),
-                          "fp64_frac": round(tr.flops / kern_s / 1e9 / FP64_PEAK_GFLOPS, 4)},
+                          "fp64_frac": round(tr.flops / kern_s / 1e9 / fp64_peak(), 4)},
                          **dram_view(ncu_traffic(kname, args.workload), tr.bytes_min, A.nnz, kern_s, hbm, pm)),
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
@@ -408,7 +476,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     if "ordering" in groups and k == 1 and eigen:
         line["ordering"] = ordering_forms(A, torch, spmv, pm, timer, stream, B, C, args.workload, args.form_steps)
     if "block" in groups and args.workload == "laplace2d_256":
-        line["forms"] = block_precision_forms(A, torch, spmv, pm, stream)
+        line["forms"] = laplace_section(torch, spmv, pm, stream, with_cpu=False)
     if args.selector:
         line["selector"] = plan_selector(args, A, timer, stream, tr, spmv)
     if rank == 0 and not args.no_cpu:
@@ -512,14 +580,14 @@ def spmm_forms(A, torch, spmv, pm, timer, stream, names):
             C = torch.empty_like(B)
             stream.wait_stream(torch.cuda.current_stream())
             tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
-            t_bound = max(tr.bytes_min / (hbm * 1e9), tr.flops / (FP64_PEAK_GFLOPS * 1e9))
+            t_bound = max(tr.bytes_min / (hbm * 1e9), tr.flops / (fp64_peak() * 1e9))
             row = {"bound_us": round(t_bound * 1e6, 1)}
             for name in names:
                 vid, sigma = VARIANTS[name]
                 p.set_variant(vid, sigma)
                 t = statistics.median(timer.run(lambda: p.apply_block(B, C, k, stream), 30, 3)["per_ms"]) / 1e3
                 row[name] = {"us": round(t * 1e6, 1), "gflops": round(tr.flops / t / 1e9, 1),
-                             "fp64_frac": round(tr.flops / t / 1e9 / FP64_PEAK_GFLOPS, 4),
+                             "fp64_frac": round(tr.flops / t / 1e9 / fp64_peak(), 4),
                              "frac_of_bound": round(t_bound / t, 4)}
             out[f"k{k}"] = row
             del B, C
@@ -609,7 +677,7 @@ def cg_forms(A, torch, spmv, pm, stream, iters: int = 50):
         flops = 2 * k * A.nnz + 10 * k * A.n_rows
         byts = cg_bytes_per_iteration(pm, A, k)
         spmm = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
-        t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (FP64_PEAK_GFLOPS * 1e9))
+        t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (fp64_peak() * 1e9))
                    + 88 * k * A.n_rows / (hbm * 1e9))
         out[f"k{k}"] = {"plan_variant": "crs_l1",
                         "us_per_iteration": round(t_it * 1e6, 1), "gflops": round(flops / t_it / 1e9, 1),
@@ -617,7 +685,7 @@ def cg_forms(A, torch, spmv, pm, stream, iters: int = 50):
                         "bound_us": round(t_bound * 1e6, 1), "frac_of_bound": round(t_bound / t_it, 4),
                         "column_iterations_per_s": round(k / t_it, 1)}
     out["hbm_peak"] = hbm
-    out["fp64_peak_gflops"] = round(FP64_PEAK_GFLOPS, 1)
+    out["fp64_peak_gflops"] = round(fp64_peak(), 1)
     out["timing"] = "host wall clock around the synchronous solve (one poll at the end), best of 3"
     return out
 
@@ -645,7 +713,7 @@ def lanczos_forms(A, torch, spmv, pm, stream, m: int = 30):
             t_it = min(ts) / m
             spmm = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k)
             byts = spmm.bytes_min + 72 * k * A.n_rows
-            t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (FP64_PEAK_GFLOPS * 1e9))
+            t_bound = (max(spmm.bytes_min / (hbm * 1e9), spmm.flops / (fp64_peak() * 1e9))
                        + 72 * k * A.n_rows / (hbm * 1e9))
             out[f"k{k}"] = {"us_per_step": round(t_it * 1e6, 1),
                             "gflops": round((2 * k * A.nnz + 8 * k * A.n_rows) / t_it / 1e9, 1),
@@ -656,13 +724,32 @@ def lanczos_forms(A, torch, spmv, pm, stream, m: int = 30):
     return out
 
 
-def block_precision_forms(A, torch, spmv, pm, stream):
-    """k right-hand sides x value storage on the L2-resident 2D Laplacian: warm
-    (back to back) and cold (L2 flushed by a 256 MB write before each launch)
-    median CUDA-event times of the plan's default kernel."""
+def laplace_section(torch, spmv, pm, stream, with_cpu: bool = True) -> dict:
+    """The 2D 5-point Laplacian on 256^2 (65,536 rows, 326,656 nonzeros; the
+    first configuration) and its k in {1, 4, 8, 16} right-hand sides with
+    FP64 and FP32-stored values (the precision / block configuration).  The
+    5 MB matrix is L2-resident, so one product is latency- and launch-bound;
+    per (k, storage) four device times are reported:
+      isolated: one launch between two events, queue empty before it;
+      back_to_back: 200 launches between two events (launch gaps included);
+      graph: 100 products captured into one CUDA graph, replayed (the
+             kernel's own latency, launch overhead taken off the host);
+      cold: one launch after a 256 MB write has flushed L2.
+    Errors per right-hand-side column against the oracle's CRS loop (FP64
+    values; the FP32-value form also against the oracle's FP32-value loop),
+    as the largest |y - y_ref| / (tol * sum_j |a_ij b_j|) of the column."""
     import gen
+    import oracle
+    A = gen.laplace2d(256)
+    hbm, _ = measured_hbm()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {}
+    out = {"workload": "laplace2d_256", "description": WORKLOADS["laplace2d_256"], "n_rows": A.n_rows,
+           "nnz": A.nnz, "timing": "median CUDA-event times (see keys); GFlop/s = 2 k nnz / time",
+           "err_bound": {"f64val": "1e-13*sum|ab| vs the FP64 oracle", "f32val": "2e-7*sum|ab| vs the FP64 oracle"}}
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
     for f32 in (False, True):
         with spmv.Plan.from_csr(A, val_fp32=f32) as p:
             for k in (1, 4, 8, 16):
@@ -670,24 +757,171 @@ def block_precision_forms(A, torch, spmv, pm, stream):
                 B = torch.from_numpy(Bh).cuda()
                 C = torch.empty((A.n_rows,) if k == 1 else (A.n_rows, k), dtype=torch.float64, device="cuda")
                 stream.wait_stream(torch.cuda.current_stream())
-                fn = (lambda: p.apply(B, C, stream)) if k == 1 else (lambda: p.apply_block(B, C, k, stream))
-                warm, cold = [], []
+
+                def fn(st=stream):
+                    (p.apply(B, C, st) if k == 1 else p.apply_block(B, C, k, st))
+                iso, cold = [], []
                 for i in range(60):
                     if i % 2:
                         with torch.cuda.stream(stream):
                             flush.zero_()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    else:
+                        stream.synchronize()
+                    e0, e1 = ev_pair()
                     e0.record(stream)
                     fn()
                     e1.record(stream)
                     stream.synchronize()
-                    (cold if i % 2 else warm).append(e0.elapsed_time(e1) / 1e3)
+                    (cold if i % 2 else iso).append(e0.elapsed_time(e1) / 1e3)
+                e0, e1 = ev_pair()
+                e0.record(stream)
+                for _ in range(200):
+                    fn()
+                e1.record(stream)
+                stream.synchronize()
+                b2b = e0.elapsed_time(e1) / 1e3 / 200
+                # 100 products in one CUDA graph, captured on a side stream
+                g = torch.cuda.CUDAGraph()
+                cap = torch.cuda.Stream()
+                cap.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.graph(g, stream=cap, capture_error_mode="thread_local"):
+                    for _ in range(100):
+                        fn(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                gts = []
+                for _ in range(7):
+                    e0, e1 = ev_pair()
+                    e0.record(stream)
+                    with torch.cuda.stream(stream):
+                        g.replay()
+                    e1.record(stream)
+                    stream.synchronize()
+                    gts.append(e0.elapsed_time(e1) / 1e3 / 100)
+                del g
+                y = C.cpu().numpy()
+                B2 = Bh.reshape(A.n_cols, k)
+                y2 = y.reshape(A.n_rows, k)
+                ref = oracle.spmm(A, B2)
+                scale = oracle.abs_scale(A, B2)
+                tol = 2e-7 if f32 else 1e-13
+                col_err = [oracle.max_err_ratio(y2[:, c], ref[:, c], scale[:, c], tol) for c in range(k)]
+                row = {}
+                if f32:
+                    ref32 = oracle.spmm(A, B2, f32val=True)
+                    row["err_ratio_vs_f32val_oracle_at_1e-13"] = round(max(
+                        oracle.max_err_ratio(y2[:, c], ref32[:, c], scale[:, c], 1e-13) for c in range(k)), 6)
                 tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k, val_bytes=4 if f32 else 8)
-                tw, tc = statistics.median(warm[5:]), statistics.median(cold[5:])
-                out[f"k{k}_{'f32' if f32 else 'f64'}val"] = {
-                    "warm_gflops": round(tr.flops / tw / 1e9, 1), "warm_us": round(tw * 1e6, 2),
-                    "cold_gflops": round(tr.flops / tc / 1e9, 1), "cold_us": round(tc * 1e6, 2),
-                    "cold_hbm_gbs": round(tr.bytes_min / tc / 1e9, 1)}
+                ti, tc, tg = statistics.median(iso[5:]), statistics.median(cold[5:]), statistics.median(gts)
+                row.update({
+                    "isolated_us": round(ti * 1e6, 2), "isolated_gflops": round(tr.flops / ti / 1e9, 1),
+                    "back_to_back_us": round(b2b * 1e6, 2), "back_to_back_gflops": round(tr.flops / b2b / 1e9, 1),
+                    "graph_us": round(tg * 1e6, 2), "graph_gflops": round(tr.flops / tg / 1e9, 1),
+                    "cold_us": round(tc * 1e6, 2), "cold_gflops": round(tr.flops / tc / 1e9, 1),
+                    "cold_hbm_gbs": round(tr.bytes_min / tc / 1e9, 1),
+                    "err_ratio_per_column": [round(e, 6) for e in col_err],
+                    "bit_identical_columns": int(sum(np.array_equal(y2[:, c], ref[:, c]) for c in range(k)))})
+                out[f"k{k}_{'f32' if f32 else 'f64'}val"] = row
+    best = min(v["graph_us"] for key, v in out.items() if key.startswith("k1_"))
+    out["roofline"] = {"bound": "latency", "note": "L2-resident: the HBM time of V_min is "
+                       f"{pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz).bytes_min / (hbm * 1e9) * 1e6:.2f} us, far "
+                       "below a kernel's launch-to-finish latency", "graph_us_k1": best}
+    if with_cpu:
+        Bh = gen.uniform(A.n_cols, seed=0)
+        ts = time_oracle(lambda: oracle.spmv(A, Bh), 20, budget_s=5.0)
+        out["cpu_baseline"] = {"value": round(2 * A.nnz / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                               "kind": "oracle", "sample": f"full k = 1 product, best of {len(ts)}"}
+    del flush
+    return out
+
+
+COST_MODEL_DIR = os.path.join(ROOT, "paper_1101_0091_gb300", "cost_models")
+
+
+def far_entries(A, reach: int = 32) -> int:
+    """Stored entries with |i - j| > reach.  A warp's 32 rows read B entries
+    inside a window of about 32 around them (8 sectors of 32 bytes), so
+    closer entries share sectors; each farther entry needs a 32-byte sector of
+    its own, one random read served by L2 at best."""
+    rows = np.repeat(np.arange(A.n_rows, dtype=np.int64), np.diff(A.row_ptr).astype(np.int64))
+    return int(np.count_nonzero(np.abs(rows - A.col_idx.astype(np.int64)) > reach))
+
+
+def eigen_section(torch, spmv, pm, timer, stream, steps: int = 50, with_ordering: bool = True,
+                  with_cpu: bool = True) -> dict:
+    """The eigenproblem-shaped matrix (6,201,600 = 400 x 15,504 rows, about
+    13.8 nonzeros per row, ten of them scattered within +-2^20): every plan
+    kernel, SELL-32 with sigma in {1, 256, 4096} among them, and the cost
+    model's choice, at k = 1 (median event time of `steps` launches).  Two
+    roofs: HBM (V_min at the measured copy peak) and the random reads of B
+    (one 32-byte sector per scattered entry at the rate spmv_probe_gather
+    measures out of an L2-resident buffer)."""
+    import gen
+    import oracle
+    from paper_1101_0091_gb300 import selector as sel
+    A = gen.eigen_shaped(6_201_600, seed=0)
+    Bh = gen.uniform(A.n_cols, seed=0)
+    B = torch.from_numpy(Bh).cuda()
+    C = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    stream.wait_stream(torch.cuda.current_stream())
+    hbm, hbm_kind = measured_hbm()
+    tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz)
+    n_far = far_entries(A)
+    req_rate = MACHINE.get("l2_gathers_per_s")
+    t_hbm = tr.bytes_min / (hbm * 1e9)
+    # requests from the SMs' L1 to L2 that no schedule avoids: one per scattered
+    # entry (its 32-byte sector of B is read by nothing else nearby) and one per
+    # 128-byte line of the compulsory streams (V_min)
+    req_min = n_far + tr.bytes_min / 128
+    t_l2 = req_min / req_rate if req_rate else None
+    out = {"workload": "eigen_6201600", "description": WORKLOADS["eigen_6201600"], "n_rows": A.n_rows, "nnz": A.nnz,
+           "algorithmic_bytes_per_launch": tr.bytes_min, "scattered_entries": n_far,
+           "l2_requests_min": int(req_min),
+           "hbm_bound_us": round(t_hbm * 1e6, 1),
+           "request_bound_us": round(t_l2 * 1e6, 1) if t_l2 else None,
+           "request_bound": "(scattered entries + V_min / 128 B) / the probe's random-read rate per SM and clock "
+                            "x SMs x max clock",
+           "timing": f"median CUDA-event time of {steps} launches, k = 1"}
+    times = {}
+    with spmv.Plan.from_csr(A) as p:
+        out["auto_variant"] = spmv.VARIANT_NAMES[p.info().variant]
+        for name, vid, sigma in sel.PLAN_VARIANTS:
+            p.set_variant(vid, sigma)
+            t = statistics.median(timer.run(lambda: p.apply(B, C, stream), steps, 3)["per_ms"]) / 1e3
+            times[name] = t
+            out[name] = {"us": round(t * 1e6, 1), "gflops": round(tr.flops / t / 1e9, 1),
+                         "hbm_frac": round(t_hbm / t, 4), "request_frac": round(t_l2 / t, 4) if t_l2 else None}
+            if name == "sell_s256":
+                out[name]["parity_max_err_ratio"] = round(oracle.max_err_ratio(
+                    C.cpu().numpy(), oracle.spmv(A, Bh), oracle.abs_scale(A, Bh), 1e-13), 6)
+        sweep = np.array([times[v[0]] for v in sel.PLAN_VARIANTS])
+        ck = os.path.join(COST_MODEL_DIR, "plan.bin")
+        if os.path.exists(ck):
+            cm = sel.CostModel.load(ck)
+            c = int(cm.select(spmv.features(A, 1))[0][0])
+            cm.close()
+            name = sel.PLAN_VARIANTS[c][0]
+            out["selector"] = {"model": "paper_1101_0091_gb300/cost_models/plan.bin", "chosen": name,
+                               "gflops_chosen": out[name]["gflops"],
+                               "gflops_default_crs_l1": out["crs_l1"]["gflops"],
+                               "best_in_sweep": sel.PLAN_VARIANTS[int(sweep.argmin())][0],
+                               "regret": round(float(sweep[c] / sweep.min() - 1), 4)}
+    best = min(times, key=times.get)
+    tb = times[best]
+    out["roofline"] = {"bound": "l2_requests", "kernel": best, "achieved_us": round(tb * 1e6, 1),
+                       "achieved": round(req_min / tb / 1e9, 2) if t_l2 else None, "unit": "1e9 requests/s",
+                       "peak": round(req_rate / 1e9, 2) if req_rate else None,
+                       "frac": round(t_l2 / tb, 4) if t_l2 else None,
+                       "hbm_achieved_gbs": round(tr.bytes_min / tb / 1e9, 1), "hbm_peak": hbm,
+                       "hbm_frac": round(t_hbm / tb, 4),
+                       "frac_of_max_bound": round(max(t_hbm, t_l2 or 0.0) / tb, 4),
+                       "traffic": ncu_traffic("sell", "eigen_6201600")}
+    out.update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
+    if with_ordering:
+        out["ordering"] = ordering_forms(A, torch, spmv, pm, timer, stream, B, C, "eigen_6201600", steps)
+    if with_cpu:
+        ts = time_oracle(lambda: oracle.spmv(A, Bh), 3, budget_s=10.0)
+        out["cpu_baseline"] = {"value": round(tr.flops / min(ts) / 1e9, 4), "unit": "GFlop/s", "cores": 1,
+                               "kind": "oracle", "sample": f"full product, best of {len(ts)}"}
     return out
 
 
@@ -699,7 +933,7 @@ def mixed_row_bound(As, kern_s, hbm) -> dict:
     t = 0.0
     for A in As:
         L = np.diff(A.row_ptr).astype(np.float64)
-        t += float(np.maximum((12 * L + 68) / (hbm * 1e9), 8 * L / (FP64_PEAK_GFLOPS * 1e9)).sum())
+        t += float(np.maximum((12 * L + 68) / (hbm * 1e9), 8 * L / (fp64_peak() * 1e9)).sum())
     return {"mixed_bound_us": round(t * 1e6, 1), "mixed_frac": round(t / kern_s, 4),
             "mixed_bound_kind": "sum over rows of max(HBM time of 12L+68 B, FP64 time of 8L flops)"}
 
@@ -741,9 +975,9 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
                    "autotuned": tuned, "l2": "inputs larger than L2, no flush",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "hbm_gbs": round(bytes_min / kern_s / 1e9, 1),
-        "roofline": {"bound": "alu", "achieved": round(achieved_gf, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-                     "unit": "GFLOP/s", "frac": round(achieved_gf / FP64_PEAK_GFLOPS, 4),
-                     "peak_kind": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+        "roofline": {"bound": "alu", "achieved": round(achieved_gf, 1), "peak": round(fp64_peak(), 1),
+                     "unit": "GFLOP/s", "frac": round(achieved_gf / fp64_peak(), 4),
+                     "peak_kind": "FP64 FMA rate, " + MACHINE["fp64_kind"],
                      "traffic": ncu_traffic("batch", args.workload), "algorithmic_bytes_per_launch": bytes_min,
                      "hbm_frac": round(bytes_min / kern_s / 1e9 / hbm, 4), "hbm_peak": hbm, "hbm_peak_kind": hbm_kind,
                      **mixed_row_bound(As, kern_s, hbm)},
@@ -788,6 +1022,8 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         line["forms"] = forms
     if args.selector:
         line["selector"] = batch_selector(args, As, batch, timer, stream, flops, spmv)
+    elif os.path.exists(os.path.join(COST_MODEL_DIR, "batch.bin")):
+        line["learned_policies"] = batch_learned(As, batch, timer, stream, flops, spmv)
     if rank == 0 and not args.no_cpu:
         import oracle
         sub = min(len(As), 64)
@@ -802,6 +1038,33 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     return line
 
 
+def batch_learned(As, batch, timer, stream, flops, spmv) -> dict:
+    """The shipped batch cost model (trained on members timed inside a mixed
+    batch) picks each member's row policy, guarded: a member leaves the
+    default sorted policy only for a predicted gain above the margin
+    calibrated on a validation batch at training time.  Whole-batch
+    time with those policies against every member on the default (median of
+    50 graph replays each)."""
+    from paper_1101_0091_gb300 import selector as sel
+    cm = sel.CostModel.load(os.path.join(COST_MODEL_DIR, "batch.bin"))
+    X = np.array([spmv.features(A, 4) for A in As])
+    choice, _ = cm.select_guarded(X, sel.BATCH_DEFAULT)
+    margin = cm.margin
+    cm.close()
+    names = [p[0] for p in sel.BATCH_POLICIES]
+    batch.set_policies([sel.BATCH_POLICIES[c][1] for c in choice])
+    t_sel = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
+    batch.set_policies([sel.BATCH_POLICIES[sel.BATCH_DEFAULT][1]] * len(As))
+    t_def = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
+    return {"model": "paper_1101_0091_gb300/cost_models/batch.bin",
+            "margin": None if margin is None or margin == float("inf") else margin,
+            "margin_kind": "calibrated on a validation batch (null: keep the default)" if margin is not None
+            else "uncalibrated default",
+            "choices": {names[v]: int((choice == v).sum()) for v in range(len(names))},
+            "gflops_learned": round(flops / t_sel / 1e9, 1), "gflops_default_sorted": round(flops / t_def / 1e9, 1),
+            "learned_over_default": round(t_def / t_sel, 4)}
+
+
 def batch_selector(args, As, batch, timer, stream, flops, spmv):
     """Cost model for batch members: trained on generated members, evaluated on
     every n-th member against the exhaustive sweep of all row policies, then
@@ -809,23 +1072,27 @@ def batch_selector(args, As, batch, timer, stream, flops, spmv):
     import tempfile
     from paper_1101_0091_gb300 import selector as sel
     t0 = time.time()
-    train = sel.build_dataset(sel.batch_training_matrices(args.selector_train), "batch", stream)
-    cm = sel.train_model(train, len(sel.BATCH_POLICIES))
+    ctx = sel.BatchContext(sel.batch_background(), stream)
+    train = sel.build_dataset(sel.batch_training_matrices(args.selector_train), "batch", stream, batch_ctx=ctx)
+    cm = sel.train_model(train, len(sel.BATCH_POLICIES), epochs=sel.BATCH_EPOCHS)
+    cal = sel.calibrate_margin(cm, sel.validation_members(), stream)
     ckpt = os.path.join(tempfile.gettempdir(), "spmv_batch_cost_model.bin")
     cm.save(ckpt)
     t_train = time.time() - t0
     idx = list(range(0, len(As), args.selector_stride))
-    ev = sel.build_dataset([As[i] for i in idx], "batch", stream)
-    choice, _ = cm.select(ev.X)
+    ev = sel.build_dataset([As[i] for i in idx], "batch", stream, batch_ctx=ctx)
+    ctx.close()
+    choice, _ = cm.select_guarded(ev.X, sel.BATCH_DEFAULT)
     names = [p[0] for p in sel.BATCH_POLICIES]
     best_fixed = int(ev.times.sum(axis=0).argmin())
     Xall = np.array([spmv.features(A, 4) for A in As])
-    ch_all, _ = cm.select(Xall)
+    ch_all, _ = cm.select_guarded(Xall, sel.BATCH_DEFAULT)
     batch.set_policies([sel.BATCH_POLICIES[c][1] for c in ch_all])
     t_sel = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
     batch.set_policies([sel.BATCH_POLICIES[sel.BATCH_DEFAULT][1]] * len(As))
     t_def = statistics.median(timer.run(lambda: batch.apply(stream), 50, 5)["per_ms"]) / 1e3
     return {"training_members": args.selector_train, "train_and_sweep_s": round(t_train, 1),
+            "guard_calibration": cal,
             "evaluated_members": len(idx), "regret_learned": sel.regret(ev.times, choice),
             "regret_default_" + names[sel.BATCH_DEFAULT]: sel.fixed_choice_regret(ev.times, sel.BATCH_DEFAULT),
             "regret_best_fixed_" + names[best_fixed]: sel.fixed_choice_regret(ev.times, best_fixed),
@@ -859,6 +1126,45 @@ def plan_selector(args, A, timer, stream, tr, spmv):
             "regret": round(float(sweep[c] / sweep.min() - 1), 4)}
 
 
+CONFIG_SECTIONS = ("laplace2d_256", "eigen_6201600", "powerlaw_batch512")
+_SECTION_ALIASES = {"laplace": "laplace2d_256", "eigen": "eigen_6201600", "batch": "powerlaw_batch512"}
+_TOP_ONLY = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "paper_context", "machine")
+
+
+def config_sections(args) -> list:
+    """The configurations measured beside the headline in one run."""
+    c = args.configs
+    if c == "auto":
+        default = (args.workload == "poisson3d_280" and args.k == 1 and args.variant == "crs_l1"
+                   and not args.fp32_val and not args.no_forms)
+        return list(CONFIG_SECTIONS) if default else []
+    if c == "none":
+        return []
+    if c == "all":
+        return list(CONFIG_SECTIONS)
+    return [_SECTION_ALIASES.get(x, x) for x in c.split(",") if x]
+
+
+def run_config(name, args, torch, spmv, pm, timer, stream, world, rank) -> dict:
+    """One configuration section of the default line, bounded in time: the 2D
+    Laplacian with k columns and both value storages (first and fourth
+    configurations), the eigenproblem-shaped matrix (third), and the uneven
+    batch (fifth; its own timed persistent launches, forms and cost model)."""
+    import types
+    if name == "laplace2d_256":
+        return laplace_section(torch, spmv, pm, stream, with_cpu=rank == 0 and not args.no_cpu)
+    if name == "eigen_6201600":
+        return eigen_section(torch, spmv, pm, timer, stream, steps=50, with_cpu=rank == 0 and not args.no_cpu)
+    if name == "powerlaw_batch512":
+        sub = types.SimpleNamespace(**vars(args))
+        sub.workload, sub.steps, sub.warmup, sub.no_forms, sub.selector = "powerlaw_batch512", 50, 5, False, False
+        sec = batch_workload(sub, torch, spmv, pm, timer, stream, world, rank)
+        for k in _TOP_ONLY:
+            sec.pop(k, None)
+        return sec
+    raise ValueError(name)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -876,10 +1182,25 @@ def main():
     spmv.load()
     stream = torch.cuda.Stream()
     timer = Timer(torch, stream, world, local)
+    machine = None if args.no_probes else probe_machine(spmv)
     if args.workload.startswith("powerlaw_batch"):
         line = batch_workload(args, torch, spmv, pm, timer, stream, world, rank)
     else:
         line = single_workload(args, torch, spmv, pm, timer, stream, world, rank)
+    if machine:
+        line["machine"] = machine
+    configs = config_sections(args)
+    if configs:
+        line["configs"] = {}
+        for name in configs:
+            t0 = time.perf_counter()
+            try:
+                sec = run_config(name, args, torch, spmv, pm, timer, stream, world, rank)
+            except Exception as e:  # the headline stays; the failed section says why
+                sec = {"error": f"{type(e).__name__}: {e}"}
+            sec["section_wall_s"] = round(time.perf_counter() - t0, 1)
+            line["configs"][name] = sec
+            torch.cuda.synchronize()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -56,7 +56,12 @@ typedef enum {
  * one fused multiply-add per stored entry (SYM: per stored off-diagonal entry
  * also one multiply for its mirror product). */
 typedef enum {
-  SPMV_VARIANT_AUTO = 0,   /* the plan's default: CRS_L1 (a tuner or the cost model may switch)  */
+  SPMV_VARIANT_AUTO = 0,   /* the plan's default, decided at creation from the matrix: SELL with  */
+                           /* sigma 256 when more than 30 % of the entries of a sample of rows   */
+                           /* are gathered at scattered addresses (entry (i, c) is regular when */
+                           /* row i-1 holds column c-1 or row i+1 holds c+1) and SELL-32-256     */
+                           /* stores at least 0.85 nonzeros per slot; CRS_L1 otherwise (a tuner  */
+                           /* or the cost model may switch)                                      */
   SPMV_CRS_STAGED = 1,     /* thread per row; each CTA's contiguous val/col tile is brought     */
                            /* into shared memory by one bulk copy (cp.async.bulk + mbarrier);   */
                            /* rows longer than 64 go to warp-per-row blocks                      */
@@ -183,7 +188,10 @@ spmv_status spmv_get_info(spmv_handle h, spmv_info* info);
 /* Launch parameters a tuner may change without touching the result.
  * prefetch_distance: each CTA of the row and SELL kernels asks the TMA engine
  * to prefetch into L2 the matrix slice of the CTA this many positions ahead
- * (cp.async.bulk.prefetch.L2); 0 disables it. */
+ * (cp.async.bulk.prefetch.L2); 0 disables it.  Default: 152 (one per SM), and
+ * 0 on matrices whose gathers are scattered (the test of SPMV_VARIANT_AUTO):
+ * their product is bound by the SMs' requests to L2, which a prefetch adds
+ * to. */
 typedef struct {
   int32_t prefetch_distance;
   int32_t reserved[7];
@@ -398,6 +406,13 @@ spmv_status spmv_model_train_step(spmv_model_handle m, const float* X_dev, const
  * float32[M x n_out]) may be NULL.  Synchronises the stream. */
 spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32_t M, int32_t* choice,
                               float* predicted, void* stream);
+/* As spmv_model_select, with a guard for a known-good default: row i takes the
+ * output of smallest prediction only if that prediction is below the
+ * prediction of output `fallback` by more than `margin` (log-time units: 0.05
+ * asks for a predicted gain above about 5 %); otherwise it takes `fallback`.
+ * fallback < 0 turns the guard off; margin >= 0. */
+spmv_status spmv_model_select_guarded(spmv_model_handle m, const double* features, int32_t M, int32_t fallback,
+                                      float margin, int32_t* choice, float* predicted, void* stream);
 /* Pick a plan's kernel with the cost model: the plan's 34 features for k
  * right-hand sides (spmv_features) go through the network (n_in must be 34),
  * output o stands for variant variants[o] with SELL sigma sigmas[o] (host
@@ -525,20 +540,25 @@ spmv_status spmv_reorder_destroy(spmv_reorder_handle h);
  * ------------------------------------------------------------------------- */
 
 /* FP64 fused multiply-add rate: every thread of a grid filling all SMs runs 8
- * independent FMA chains.  *gflops = 2 x FMAs / time (1e9 flop/s); *ms the
- * best launch time; *sm_count the device's multiprocessors (any output may be
- * NULL).  Bounds the products with k >= 2 columns, where each stored entry
- * needs k FMAs (and the batch, the solvers). */
-spmv_status spmv_probe_fp64(int32_t reps, double* gflops, double* ms, int32_t* sm_count);
+ * independent FMA chains with register operands.  *gflops = 2 x FMAs / time
+ * (1e9 flop/s); *ms the best launch time; *sm_count the device's
+ * multiprocessors; *sm_mhz the SM clock during that launch (clock cycles over
+ * %globaltimer nanoseconds, averaged over the CTAs), so that
+ * gflops / (2 x sm_count x sm_mhz) is the FMA rate per SM and clock.  Any
+ * output may be NULL.  Bounds the products with k >= 2 columns, where each
+ * stored entry needs k FMAs (and the batch, the solvers). */
+spmv_status spmv_probe_fp64(int32_t reps, double* gflops, double* ms, int32_t* sm_count, double* sm_mhz);
 
 /* Random 8-byte read rate: a grid filling all SMs reads uniformly random
  * entries of a zero-filled buffer of n_elems doubles (1 <= n_elems <=
  * 2^31-1) with read-only loads, 8 independent reads in flight per thread.
- * *gathers_per_s = reads / time; *ms the best launch time.  A buffer the size
- * of B of the eigenproblem-shaped workload (6,201,600 doubles, 50 MB) stays in
- * L2: the rate bounds a product whose B gathers are scattered (each read moves
- * a whole 32-byte sector for 8 useful bytes). */
-spmv_status spmv_probe_gather(int64_t n_elems, int32_t reps, double* gathers_per_s, double* ms);
+ * *gathers_per_s = reads / time; *ms the best launch time; *sm_mhz the SM
+ * clock during it (as for spmv_probe_fp64).  A buffer the size of B of the
+ * eigenproblem-shaped workload (6,201,600 doubles, 50 MB) stays in L2; every
+ * read of a sector that the SM's L1 does not hold costs one request from the
+ * SM's L1 to the crossbar, and those requests, about one per SM and clock,
+ * bound a product whose B gathers are scattered. */
+spmv_status spmv_probe_gather(int64_t n_elems, int32_t reps, double* gathers_per_s, double* ms, double* sm_mhz);
 
 /* ----------------------------------------------------------------------------
  * Matrix features read by the cost model (host computation, no device use).

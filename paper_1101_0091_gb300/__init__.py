@@ -39,7 +39,8 @@ from ._binding_solver import (Solver, spmv_cg_solve, spmv_cg_summary, spmv_lancz
                              spmv_solver_create, spmv_solver_destroy)
 from ._binding_model import (spmv_model_adam_step, spmv_model_create, spmv_model_destroy,  # noqa: F401,E402
                              spmv_model_forward, spmv_model_get_params, spmv_model_info, spmv_model_load,
-                             spmv_model_loss_grad, spmv_model_save, spmv_model_select, spmv_model_set_normalizer,
+                             spmv_model_loss_grad, spmv_model_save, spmv_model_select, spmv_model_select_guarded,
+                             spmv_model_set_normalizer,
                              spmv_model_set_params, spmv_model_train_step)
 
 LANE_VARIANTS = {1: SPMV_CRS_L1, 2: SPMV_CRS_L2, 4: SPMV_CRS_L4, 8: SPMV_CRS_L8, 16: SPMV_CRS_L16,

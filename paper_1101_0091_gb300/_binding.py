@@ -74,8 +74,8 @@ _SIGS = {
     "spmv_split_build_host": ([_i64, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
     "spmv_sym_build_host": ([_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
-    "spmv_probe_fp64": ([_i32, _vp, _vp, _vp], ctypes.c_int),
-    "spmv_probe_gather": ([_i64, _i32, _vp, _vp], ctypes.c_int),
+    "spmv_probe_fp64": ([_i32, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_probe_gather": ([_i64, _i32, _vp, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -234,13 +234,14 @@ def spmv_selftest_wait_timeout(limit_us: int) -> None:
 
 def spmv_probe_fp64(reps: int = 5) -> dict:
     """FP64 FMA rate of the current device (spmv_probe_fp64)."""
-    g, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
-    _check(load().spmv_probe_fp64(reps, ctypes.byref(g), ctypes.byref(ms), ctypes.byref(sms)))
-    return {"gflops": g.value, "ms": ms.value, "sm_count": sms.value}
+    g, ms, sms, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().spmv_probe_fp64(reps, ctypes.byref(g), ctypes.byref(ms), ctypes.byref(sms), ctypes.byref(mhz)))
+    return {"gflops": g.value, "ms": ms.value, "sm_count": sms.value, "sm_mhz": mhz.value,
+            "fma_per_clock_per_sm": g.value * 1e3 / (2 * sms.value * mhz.value) if mhz.value > 0 else None}
 
 
 def spmv_probe_gather(n_elems: int, reps: int = 5) -> dict:
     """Random 8-byte read rate out of a buffer of n_elems doubles (spmv_probe_gather)."""
-    r, ms = ctypes.c_double(), ctypes.c_double()
-    _check(load().spmv_probe_gather(n_elems, reps, ctypes.byref(r), ctypes.byref(ms)))
-    return {"gathers_per_s": r.value, "ms": ms.value}
+    r, ms, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().spmv_probe_gather(n_elems, reps, ctypes.byref(r), ctypes.byref(ms), ctypes.byref(mhz)))
+    return {"gathers_per_s": r.value, "ms": ms.value, "sm_mhz": mhz.value}

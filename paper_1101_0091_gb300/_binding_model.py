@@ -21,6 +21,7 @@ _SIGS = {
                              ctypes.c_int),
     "spmv_model_train_step": ([_vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp], ctypes.c_int),
     "spmv_model_select": ([_vp, _vp, _i32, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_model_select_guarded": ([_vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "spmv_model_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "spmv_model_load": ([_P(_vp), ctypes.c_char_p], ctypes.c_int),
     "spmv_model_destroy": ([_vp], ctypes.c_int),
@@ -107,6 +108,18 @@ def spmv_model_select(m, features: np.ndarray, stream: int = 0):
     choice = np.empty(X.shape[0], dtype=np.int32)
     pred = np.empty((X.shape[0], V), dtype=np.float32)
     _check(_lib().spmv_model_select(m, X.ctypes.data, X.shape[0], choice.ctypes.data, pred.ctypes.data, stream))
+    return choice, pred
+
+
+def spmv_model_select_guarded(m, features: np.ndarray, fallback: int, margin: float, stream: int = 0):
+    X = np.ascontiguousarray(features, dtype=np.float64)
+    if X.ndim == 1:
+        X = X.reshape(1, -1)
+    F, H, V, _, _ = spmv_model_info(m)
+    choice = np.empty(X.shape[0], dtype=np.int32)
+    pred = np.empty((X.shape[0], V), dtype=np.float32)
+    _check(_lib().spmv_model_select_guarded(m, X.ctypes.data, X.shape[0], fallback, margin, choice.ctypes.data,
+                                            pred.ctypes.data, stream))
     return choice, pred
 
 

@@ -90,6 +90,10 @@ struct spmv_plan {
   uint64_t generation = 0;  // bumped whenever the kernel, its arrays or its launch parameters change
   spmv_options opt{};
   int variant = SPMV_CRS_STAGED;
+  // what AUTO runs: SELL-32-256 on matrices whose rows gather at scattered
+  // addresses (and pack well into SELL), CRS_L1 otherwise
+  double scattered = 0.0;
+  bool auto_sell = false;
   HostCsr host;
   DevArena arena;
   CsrDev A;            // the whole matrix
@@ -287,7 +291,10 @@ static spmv_status build_sym_dev(spmv_plan* p) {
 }
 
 static spmv_status prepare_variant(spmv_plan* p, int variant, int sigma) {
-  if (variant == SPMV_VARIANT_AUTO) variant = SPMV_CRS_L1;
+  if (variant == SPMV_VARIANT_AUTO) {
+    variant = p->auto_sell ? SPMV_SELL : SPMV_CRS_L1;
+    sigma = p->auto_sell ? 256 : sigma;
+  }
   if (variant < SPMV_CRS_STAGED || variant >= SPMV_N_VARIANTS)
     return fail(SPMV_ERR_ARG, "unknown variant " + std::to_string(variant));
   if (variant == SPMV_CRS_STAGED && !p->blocks_built) {
@@ -372,7 +379,12 @@ spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, int64_
     return fail(SPMV_ERR_OOM, "host allocation failed");
   }
   p->opt = o;
-  p->tuning.prefetch_distance = kDefaultPrefetch;
+  // Scattered gathers are bound by the SM's requests to L2, not by HBM: there
+  // the L2 prefetch of the matrix slices ahead only adds requests (SELL-32-256
+  // on the eigenproblem-shaped matrix: 306 -> 287 us without it).
+  p->scattered = scattered_fraction(p->host.row_ptr.data(), p->host.col.data(), n_rows);
+  p->auto_sell = p->scattered > kAutoScattered && sell_fill(p->host.row_ptr.data(), n_rows, 256) >= kAutoSellFill;
+  p->tuning.prefetch_distance = p->scattered > kAutoScattered ? 0 : kDefaultPrefetch;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   auto cleanup = [&](spmv_status st) {

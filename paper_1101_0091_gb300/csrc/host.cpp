@@ -2,6 +2,7 @@
 // blocks of CRS_STAGED, SELL-C-sigma, the local/halo split, and the feature
 // vector read by the cost model.  One-time work at plan creation.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -149,6 +150,55 @@ void build_sell(const HostCsr& A, int64_t C, int64_t sigma, SellHost* out) {
       }
     }
   }
+}
+
+// Fraction of the stored entries of a sample of rows that consecutive rows
+// gather at scattered addresses: entry (i, c) counts as regular when row i-1
+// holds column c-1 or row i+1 holds column c+1 (a stencil or a band moves by
+// one column per row, so a warp of consecutive rows reads consecutive B
+// entries), and as scattered otherwise.  At most about 4096 rows, evenly
+// spaced, so that the result is deterministic and cheap on any matrix.
+double scattered_fraction(const int32_t* rp, const int32_t* col, int64_t n_rows) {
+  if (n_rows < 3) return 0.0;
+  const int64_t step = std::max<int64_t>(1, (n_rows - 2) / 4096);
+  std::vector<int32_t> prev, next;
+  int64_t total = 0, scattered = 0;
+  for (int64_t i = 1; i + 1 < n_rows; i += step) {
+    prev.assign(col + rp[i - 1], col + rp[i]);
+    next.assign(col + rp[i + 1], col + rp[i + 2]);
+    std::sort(prev.begin(), prev.end());
+    std::sort(next.begin(), next.end());
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j) {
+      const int32_t c = col[j];
+      const bool reg = std::binary_search(prev.begin(), prev.end(), c - 1) ||
+                       std::binary_search(next.begin(), next.end(), c + 1);
+      ++total;
+      if (!reg) ++scattered;
+    }
+  }
+  return total ? (double)scattered / (double)total : 0.0;
+}
+
+// Fill of SELL-32-sigma (nonzeros over stored slots) from the row lengths
+// alone: rows sorted by descending length inside sigma-windows, 32 per chunk,
+// a chunk as long as its longest row.  1.0 for an empty matrix.
+double sell_fill(const int32_t* rp, int64_t n_rows, int64_t sigma) {
+  if (sigma < 1) sigma = 1;
+  std::vector<int32_t> len;
+  int64_t slots = 0;
+  for (int64_t w0 = 0; w0 < n_rows; w0 += sigma) {
+    const int64_t w1 = std::min(n_rows, w0 + sigma);
+    len.resize((size_t)(w1 - w0));
+    for (int64_t r = w0; r < w1; ++r) len[(size_t)(r - w0)] = rp[r + 1] - rp[r];
+    if (sigma > 1) std::sort(len.begin(), len.end(), std::greater<int32_t>());
+    for (size_t c = 0; c < len.size(); c += kSellC) {
+      int32_t mx = 0;
+      for (size_t t = c; t < std::min(len.size(), c + kSellC); ++t) mx = std::max(mx, len[t]);
+      slots += (int64_t)kSellC * mx;
+    }
+  }
+  const int64_t nnz = rp[n_rows];
+  return slots ? (double)nnz / (double)slots : 1.0;
 }
 
 // Local/halo split at column h (Sec. 3.1): local = entries with col < h over all

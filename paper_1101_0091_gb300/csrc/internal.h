@@ -79,6 +79,16 @@ bool validate_permutation(int64_t n, const int32_t* perm, std::vector<int32_t>* 
 // A' = P A P^T: row r of A' is row perm[r] of A, columns relabelled by inv and sorted (stable).
 void permute_csr(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, const int32_t* perm,
                  const std::vector<int32_t>& inv, int32_t* out_row_ptr, int32_t* out_col, double* out_val);
+// AUTO: a matrix whose sampled entries are scattered beyond this share (see
+// scattered_fraction) runs without the L2 prefetch, and runs SELL-32-256 when
+// that format stores at least kAutoSellFill nonzeros per slot.
+constexpr double kAutoScattered = 0.3;
+constexpr double kAutoSellFill = 0.85;
+
+// Share of a row sample's entries gathered at scattered addresses by consecutive rows (see host.cpp).
+double scattered_fraction(const int32_t* row_ptr, const int32_t* col, int64_t n_rows);
+// Nonzeros over stored slots of SELL-32-sigma, from the row lengths.
+double sell_fill(const int32_t* row_ptr, int64_t n_rows, int64_t sigma);
 void compute_features(int64_t n_rows, int64_t n_cols, const int32_t* row_ptr, const int32_t* col,
                       int k, double* f);
 

@@ -306,9 +306,11 @@ spmv_status spmv_model_train_step(spmv_model_handle m, const float* X_dev, const
   return spmv_model_adam_step(m, nullptr, lr, 0.9f, 0.999f, 1e-8f, stream);
 }
 
-spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32_t M, int32_t* choice,
-                              float* predicted, void* stream) {
+spmv_status spmv_model_select_guarded(spmv_model_handle m, const double* features, int32_t M, int32_t fallback,
+                                      float margin, int32_t* choice, float* predicted, void* stream) {
   if (!m || !features || !choice || M < 1) return fail(SPMV_ERR_ARG, "bad argument");
+  if (fallback >= m->V) return fail(SPMV_ERR_ARG, "fallback output out of range");
+  if (!(margin >= 0.0f)) return fail(SPMV_ERR_ARG, "margin must be >= 0");
   spmv_status st = ensure_cap(m, M);
   if (st != SPMV_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -321,13 +323,21 @@ spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32
   SPMV_CUDA(cudaMemcpyAsync(y.data(), m->Y, sizeof(float) * y.size(), cudaMemcpyDeviceToHost, s));
   SPMV_CUDA(cudaStreamSynchronize(s));
   for (int32_t i = 0; i < M; ++i) {
+    const float* yi = y.data() + (size_t)i * m->V;
     int best = 0;
     for (int v = 1; v < m->V; ++v)
-      if (y[(size_t)i * m->V + v] < y[(size_t)i * m->V + best]) best = v;
+      if (yi[v] < yi[best]) best = v;
+    // the guard: leave the fallback only for a predicted gain above the margin
+    if (fallback >= 0 && !(yi[best] < yi[fallback] - margin)) best = fallback;
     choice[i] = best;
   }
   if (predicted) std::memcpy(predicted, y.data(), sizeof(float) * y.size());
   return SPMV_OK;
+}
+
+spmv_status spmv_model_select(spmv_model_handle m, const double* features, int32_t M, int32_t* choice,
+                              float* predicted, void* stream) {
+  return spmv_model_select_guarded(m, features, M, -1, 0.0f, choice, predicted, stream);
 }
 
 // Checkpoint: magic, sizes, Adam step, normalizer, parameters, Adam moments.

@@ -217,6 +217,25 @@ def test_set_variant_switches(lib):
             assert_close(run(p, B), A, B)
 
 
+@pytest.mark.parametrize("name,scattered", [("eigen", True), ("poisson40", False), ("laplace256", False),
+                                             ("integer", True)])
+def test_auto_variant_follows_the_gather_pattern(lib, name, scattered):
+    """AUTO runs SELL-32-256 without the L2 prefetch on matrices whose rows
+    gather at scattered addresses (the eigenproblem-shaped matrix, a random
+    sparse matrix: SELL-32-256 fills its slots well on both), and CRS_L1 with
+    the prefetch on stencils; either way the product matches the oracle."""
+    A = case(name)
+    B = (np.random.default_rng(5).integers(-1024, 1025, A.n_cols).astype(np.float64) if name == "integer"
+         else gen.uniform(A.n_cols, seed=5))
+    with lib.Plan.from_csr(A) as p:
+        i, t = p.info(), p.tuning()
+        if scattered:
+            assert (i.variant, i.sell_sigma, t.prefetch_distance) == (lib.SPMV_SELL, 256, 0)
+        else:
+            assert (i.variant, t.prefetch_distance) == (lib.SPMV_CRS_L1, 152)
+        assert_close(run(p, B), A, B, exact=(name == "integer"))
+
+
 def test_error_paths(lib):
     A = case("ragged")
     with lib.Plan.from_csr(A, max_k=4) as p:
@@ -302,6 +321,7 @@ def test_zero_initialised_options_build_the_default_plan(lib):
             infos.append((i.variant, i.val_fp32, i.n_halo_rows, i.halo_nnz, i.sell_sigma))
         finally:
             lib.spmv_destroy(h)
-    assert infos[0] == infos[1] == infos[2] == (lib.SPMV_CRS_L1, 0, 0, 0, 0)
+    assert infos[0] == infos[1] == infos[2]
+    assert infos[0][1:4] == (0, 0, 0)            # FP64 values, no split
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     assert_close(outs[0], A, gen.uniform(A.n_cols, seed=3))
