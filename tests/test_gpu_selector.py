@@ -130,3 +130,51 @@ def test_selector_across_right_hand_side_counts(lib):
           "time ratio", t_learned / t_default)
     assert t_learned <= t_default
     assert selector.regret(test.times, choice)["total"] < 0.25
+
+
+def test_guarded_selection(lib):
+    """spmv_model_select_guarded keeps the fallback output unless the network
+    predicts a gain above the margin: a network whose weights are zero predicts
+    its output biases for every row, so the outcome is fixed by hand."""
+    from paper_1101_0091_gb300 import selector
+    F, H, V = selector.N_FEATURES, 8, 4
+    n = H * F + H + H * H + H + V * H + V
+    params = np.zeros(n, np.float32)
+    X = np.random.default_rng(0).standard_normal((3, F))
+    for bias, margin, want in (([0.0, -0.02, 0.1, 0.3], 0.05, 0),    # gain 0.02 < margin: fallback
+                               ([0.0, -0.08, 0.1, 0.3], 0.05, 1),    # gain 0.08 > margin: the argmin
+                               ([0.2, -0.02, 0.1, 0.3], 0.05, 1),    # the fallback is itself beaten by 0.22
+                               ([0.0, -0.02, 0.1, 0.3], 0.0, 1)):    # no margin: plain argmin
+        params[-V:] = bias
+        h = lib.spmv_model_create(F, H, V, params)
+        try:
+            choice, pred = lib.spmv_model_select_guarded(h, X, 0, margin)
+            assert choice.tolist() == [want] * 3 and np.allclose(pred, np.array(bias, np.float32))
+            assert lib.spmv_model_select(h, X)[0].tolist() == [int(np.argmin(bias))] * 3
+        finally:
+            lib.spmv_model_destroy(h)
+
+
+def test_learned_batch_policies_do_not_lose_to_the_default(lib):
+    """The batch cost model, trained on members timed inside a mixed batch
+    (not replicated alone), with its guard margin calibrated on a validation
+    batch (the smallest margin whose choices do not slow that whole batch,
+    else keep the default), gives a held-out batch of uneven members (seeds
+    of neither set) a whole-batch time no worse than every member on the
+    default policy (median of 30 graph replays each, 2 % for timing noise)."""
+    import torch
+    from paper_1101_0091_gb300 import selector as sel
+    stream = torch.cuda.Stream()
+    ctx = sel.BatchContext(sel.batch_background(32, seed=5000), stream)
+    data = sel.build_dataset(sel.batch_training_matrices(100, seed=1000), "batch", stream, batch_ctx=ctx)
+    ctx.close()
+    train_best = np.bincount(data.times.argmin(axis=1), minlength=7).tolist()
+    cm = sel.train_model(data, len(sel.BATCH_POLICIES), epochs=sel.BATCH_EPOCHS)
+    cal = sel.calibrate_margin(cm, sel.validation_members(48, seed=9000), stream)
+    held = [gen.powerlaw_batch_member(m, seed=777) for m in range(96)]
+    choice, _ = cm.select_guarded(np.array([lib.features(A, 4) for A in held]), sel.BATCH_DEFAULT)
+    cm.close()
+    t_learned = sel.batch_time(held, [sel.BATCH_POLICIES[c][1] for c in choice], stream)
+    t_default = sel.batch_time(held, [sel.BATCH_POLICIES[sel.BATCH_DEFAULT][1]] * len(held), stream)
+    assert t_learned <= 1.02 * t_default, (t_learned, t_default, np.bincount(choice, minlength=7).tolist(),
+                                           train_best, cal)
