@@ -938,6 +938,22 @@ def mixed_row_bound(As, kern_s, hbm) -> dict:
             "mixed_bound_kind": "sum over rows of max(HBM time of 12L+68 B, FP64 time of 8L flops)"}
 
 
+def random_dram_bound(As, bytes_min, hbm, kern_s, k: int = 4) -> dict:
+    """A DRAM bound that counts how B is read: each member's B block (8k bytes
+    per column) is fetched from HBM once, in the random order of its columns,
+    as 64-byte blocks at the random-read rate the HBM probe measures in this
+    run; the rest of V_min streams at the copy peak; the two share DRAM time,
+    so their times add."""
+    rate = MACHINE.get("dram_gathers_per_s")
+    if not rate:
+        return {}
+    b_bytes = sum(8 * k * A.n_cols for A in As)
+    t = (b_bytes / 64) / rate + (bytes_min - b_bytes) / (hbm * 1e9)
+    return {"random_dram_bound_us": round(t * 1e6, 1), "random_dram_frac": round(t / kern_s, 4),
+            "random_dram_bound_kind": "B blocks as 64-byte random fetches at the probe's HBM random-read rate "
+                                      "+ the rest of V_min at the copy peak"}
+
+
 def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     As, Bhs = batch_members(args.batch_count)
     nnz = sum(A.nnz for A in As)
@@ -964,6 +980,7 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     kern_s = statistics.mean(r["per_ms"]) / 1e3
     bytes_min = sum(pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=4).bytes_min for A in As)
     hbm, hbm_kind = measured_hbm()
+    rand_dram = random_dram_bound(As, bytes_min, hbm, kern_s)
     achieved_gf = flops / kern_s / 1e9
     line = {
         "metric": METRIC, "value": round(replica_value(flops, t_step, world) / 1e9, 3), "unit": "GFlop/s",
@@ -980,7 +997,7 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
                      "peak_kind": "FP64 FMA rate, " + MACHINE["fp64_kind"],
                      "traffic": ncu_traffic("batch", args.workload), "algorithmic_bytes_per_launch": bytes_min,
                      "hbm_frac": round(bytes_min / kern_s / 1e9 / hbm, 4), "hbm_peak": hbm, "hbm_peak_kind": hbm_kind,
-                     **mixed_row_bound(As, kern_s, hbm)},
+                     **mixed_row_bound(As, kern_s, hbm), **rand_dram},
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
         "wall_s_timed": round(r["wall_s"], 4),
