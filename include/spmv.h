@@ -107,6 +107,12 @@ typedef struct {
   int32_t val_fp32;
   int64_t device_bytes;     /* device memory held by the plan                                   */
   int64_t sym_nnz;          /* stored entries of the SPMV_SYM triangle (0 if not built)         */
+  double scattered;         /* share of the sampled entries gathered at scattered addresses     */
+                            /* (the test of SPMV_VARIANT_AUTO: about 4096 evenly spaced rows    */
+                            /* i = 1, 1 + s, ... with s = max(1, (n_rows - 2) / 4096), i <      */
+                            /* n_rows - 1; entry (i, c) regular when row i-1 holds c-1 or row   */
+                            /* i+1 holds c+1)                                                   */
+  double sell256_fill;      /* nonzeros per stored slot of SELL-32-256 (from the row lengths)    */
 } spmv_info;
 
 /* Default options: AUTO, sigma 1, FP64 values, max_k 16, no split (a zero-initialised
@@ -348,8 +354,11 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b);
  * with lanes[m] lanes per row (1, 2, 4, 8, 16 or 32; NULL: 1) in one launch of
  * the persistent batch kernel (atomic work counter).  All per-member arrays
  * are HOST arrays of `count` entries; the pointers in them are DEVICE pointers
- * of the current device; ldb/ldc NULL means k.  Results are the same as
- * spmv_batch_apply with the matching fixed policy.
+ * of the current device; ldb/ldc NULL means k.  A member with rows needs
+ * non-NULL row_ptr, col, val, B and C pointers (else SPMV_ERR_ARG; every
+ * argument is checked before the first CUDA call).  Results are the same,
+ * bit for bit, as spmv_batch_apply with the fixed policy of the same lanes
+ * per row (there is none for 16 lanes).
  *
  * Scratch: one static 8 MiB device array per device that loads the library,
  * held until the process exits, holding the work counter, the member table and

@@ -47,7 +47,8 @@ class spmv_info(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("sell_sigma", ctypes.c_int32), ("sell_slots", ctypes.c_int64),
                 ("sell_chunks", ctypes.c_int64), ("n_halo_rows", ctypes.c_int64), ("halo_nnz", ctypes.c_int64),
                 ("n_row_blocks", ctypes.c_int64), ("tile_nnz", ctypes.c_int32), ("val_fp32", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64), ("sym_nnz", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("sym_nnz", ctypes.c_int64), ("scattered", ctypes.c_double),
+                ("sell256_fill", ctypes.c_double)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64

@@ -93,6 +93,7 @@ struct spmv_plan {
   // what AUTO runs: SELL-32-256 on matrices whose rows gather at scattered
   // addresses (and pack well into SELL), CRS_L1 otherwise
   double scattered = 0.0;
+  double fill256 = 1.0;
   bool auto_sell = false;
   HostCsr host;
   DevArena arena;
@@ -383,7 +384,8 @@ spmv_status spmv_create(spmv_handle* out, int64_t n_rows, int64_t n_cols, int64_
   // the L2 prefetch of the matrix slices ahead only adds requests (SELL-32-256
   // on the eigenproblem-shaped matrix: 306 -> 287 us without it).
   p->scattered = scattered_fraction(p->host.row_ptr.data(), p->host.col.data(), n_rows);
-  p->auto_sell = p->scattered > kAutoScattered && sell_fill(p->host.row_ptr.data(), n_rows, 256) >= kAutoSellFill;
+  p->fill256 = sell_fill(p->host.row_ptr.data(), n_rows, 256);
+  p->auto_sell = p->scattered > kAutoScattered && p->fill256 >= kAutoSellFill;
   p->tuning.prefetch_distance = p->scattered > kAutoScattered ? 0 : kDefaultPrefetch;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -603,6 +605,8 @@ spmv_status spmv_get_info(spmv_handle h, spmv_info* info) {
   info->val_fp32 = h->opt.val_fp32;
   info->device_bytes = h->arena.bytes;
   info->sym_nnz = h->sym.row_ptr ? h->sym.nnz : 0;
+  info->scattered = h->scattered;
+  info->sell256_fill = h->fill256;
   return SPMV_OK;
 }
 

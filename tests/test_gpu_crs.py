@@ -236,6 +236,42 @@ def test_auto_variant_follows_the_gather_pattern(lib, name, scattered):
         assert_close(run(p, B), A, B, exact=(name == "integer"))
 
 
+def _auto_analysis(A):
+    """The AUTO test restated from its definition: about 4096 evenly spaced
+    sample rows; an entry (i, c) is regular when row i-1 holds column c-1 or
+    row i+1 holds c+1; and the fill of SELL-32-256 from the row lengths."""
+    n = A.n_rows
+    tot = sc = 0
+    if n >= 3:
+        step = max(1, (n - 2) // 4096)
+        for i in range(1, n - 1, step):
+            prev = set(A.col_idx[A.row_ptr[i - 1]:A.row_ptr[i]].tolist())
+            nxt = set(A.col_idx[A.row_ptr[i + 1]:A.row_ptr[i + 2]].tolist())
+            for c in A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]].tolist():
+                tot += 1
+                sc += not ((c - 1) in prev or (c + 1) in nxt)
+    L = np.diff(A.row_ptr).astype(np.int64)
+    slots = 0
+    for w in range(0, n, 256):
+        lw = np.sort(L[w:w + 256])[::-1]
+        slots += sum(32 * int(lw[c:c + 32].max()) for c in range(0, len(lw), 32))
+    return (sc / tot if tot else 0.0), (A.nnz / slots if slots else 1.0)
+
+
+@pytest.mark.parametrize("name", ["eigen", "poisson40", "laplace256", "integer", "powerlaw", "ragged"])
+def test_auto_analysis_reported_in_info(lib, name):
+    """spmv_info reports the two numbers AUTO decides on; they equal the rule
+    restated in Python (the sample, the counts and the fill are exact)."""
+    A = case(name)
+    want_sc, want_fill = _auto_analysis(A)
+    with lib.Plan.from_csr(A) as p:
+        i = p.info()
+        assert i.scattered == pytest.approx(want_sc, rel=1e-14, abs=0)
+        assert i.sell256_fill == pytest.approx(want_fill, rel=1e-14, abs=0)
+        auto_sell = i.scattered > 0.3 and i.sell256_fill >= 0.85
+        assert (i.variant == lib.SPMV_SELL) == auto_sell
+
+
 def test_error_paths(lib):
     A = case("ragged")
     with lib.Plan.from_csr(A, max_k=4) as p:
