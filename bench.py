@@ -905,6 +905,19 @@ def eigen_section(torch, spmv, pm, timer, stream, steps: int = 50, with_ordering
                                "gflops_default_crs_l1": out["crs_l1"]["gflops"],
                                "best_in_sweep": sel.PLAN_VARIANTS[int(sweep.argmin())][0],
                                "regret": round(float(sweep[c] / sweep.min() - 1), 4)}
+    # FP32-stored values (FP64 accumulation) under AUTO: 8 instead of 12 streamed bytes per slot
+    with spmv.Plan.from_csr(A, val_fp32=True) as p32:
+        t32 = statistics.median(timer.run(lambda: p32.apply(B, C, stream), steps, 3)["per_ms"]) / 1e3
+        y32 = C.cpu().numpy()
+        scale = oracle.abs_scale(A, Bh)
+        tr32 = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4)
+        out["auto_fp32val"] = {
+            "variant": spmv.VARIANT_NAMES[p32.info().variant], "us": round(t32 * 1e6, 1),
+            "gflops": round(tr.flops / t32 / 1e9, 1), "hbm_gbs": round(tr32.bytes_min / t32 / 1e9, 1),
+            "err_ratio_vs_f64_oracle_at_2e-7": round(oracle.max_err_ratio(y32, oracle.spmv(A, Bh), scale, 2e-7), 4),
+            "err_ratio_vs_f32val_oracle_at_1e-13": round(oracle.max_err_ratio(
+                y32, oracle.spmm(A, Bh.reshape(-1, 1), f32val=True)[:, 0], scale, 1e-13), 4),
+            "over_crs_l1_f64": round(times["crs_l1"] / t32, 3)}
     best = min(times, key=times.get)
     tb = times[best]
     out["roofline"] = {"bound": "l2_requests", "kernel": best, "achieved_us": round(tb * 1e6, 1),
