@@ -193,6 +193,20 @@ KERNEL_SOURCES = {"crs_l1": ["k_lanes.cu", "device.cuh", "layout.h"],
                   "batch": ["batch_kernel.cuh", "batch.cu", "device.cuh", "layout.h"]}
 
 
+def ncu_record(kernel: str, workload: str) -> dict:
+    """The committed ncu record of a kernel on a workload, if it was taken on the
+    current kernel sources (else {})."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        e = json.load(f).get(f"{kernel}/{workload}")
+    src = KERNEL_SOURCES.get(kernel.split("_s")[0] if kernel.startswith("sell") else kernel)
+    if not e or not src or e.get("source_fingerprint") != kernel_fingerprint(src):
+        return {}
+    return e
+
+
 def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
@@ -928,6 +942,16 @@ def eigen_section(torch, spmv, pm, timer, stream, steps: int = 50, with_ordering
                        "hbm_frac": round(t_hbm / tb, 4),
                        "frac_of_max_bound": round(max(t_hbm, t_l2 or 0.0) / tb, 4),
                        "traffic": ncu_traffic("sell", "eigen_6201600")}
+    rec = ncu_record("sell", "eigen_6201600")
+    if rec.get("l2_requests_per_launch") and req_rate and "sell_s256" in times:
+        # all L2 requests of SELL-32-256 (the SMs' and the die-to-die fabric's, one ncu launch)
+        # over its time here, against the L2-resident probe's request rate
+        ts = times["sell_s256"]
+        out["roofline"]["sell_s256_l2_requests"] = {
+            "sm": rec["sm_requests_per_launch"], "fabric": rec["fabric_requests_per_launch"],
+            "all": rec["l2_requests_per_launch"],
+            "rate_per_s": round(rec["l2_requests_per_launch"] / ts / 1e9, 1),
+            "frac_of_probe_rate": round(rec["l2_requests_per_launch"] / ts / req_rate, 4)}
     out.update(sym_forms(A, torch, spmv, pm, timer, stream, B, C))
     if with_ordering:
         out["ordering"] = ordering_forms(A, torch, spmv, pm, timer, stream, B, C, "eigen_6201600", steps)
