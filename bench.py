@@ -137,6 +137,8 @@ def parse():
     ap.add_argument("--prefetch", type=int, default=None,
                     help="L2 prefetch distance of the timed plan (default: the plan's own choice)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--batch-config", default=None,
+                    help="item_nnz,schedule,ctas_per_sm of the batched launch instead of the autotuner's choice")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison of forms")
@@ -1008,7 +1010,11 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
     batch = spmv.Batch(plans, 4, [spmv.SPMV_BATCH_SORTED] * len(As))
     batch.set_io(Bs, Cs)
     tuned = None
-    if not args.no_autotune:
+    if args.batch_config:
+        it, sc, ct = (int(x) for x in args.batch_config.split(","))
+        batch.set_config(item_nnz=it, schedule=sc, ctas_per_sm=ct)
+        tuned = {"item_nnz": it, "schedule": ["static", "atomic"][sc], "ctas_per_sm": ct, "source": "--batch-config"}
+    elif not args.no_autotune:
         best, times = batch.autotune(stream, reps=3)
         tuned = {"item_nnz": best.item_nnz, "schedule": ["static", "atomic"][best.schedule],
                  "ctas_per_sm": best.ctas_per_sm}
