@@ -89,7 +89,7 @@ def probe_machine(spmv) -> dict:
                 buffer the size of the eigenproblem matrix's B
                 (spmv_probe_gather); each is one request from the SM's L1 to
                 the crossbar, the port that bounds scattered gathers.
-    The HBM copy peak comes from the driver's measurement."""
+    The HBM copy peak is the measured one of MEASURED_PEAKS.json."""
     f = spmv.spmv_probe_fp64(5)
     l2 = spmv.spmv_probe_gather(6_201_600, 5)
     dram = spmv.spmv_probe_gather(1 << 28, 3)
