@@ -315,6 +315,26 @@ spmv_status spmv_batch_apply(spmv_batch_handle b, void* stream);
 spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
                                   void* stream);
 
+/* Pipelined end-to-end batched products from PAGE-LOCKED host buffers (the
+ * paper's overlap of transfers and computation, Sec. 3.2, applied to the host
+ * link).  Each call enqueues one step and returns: every member's B_host[m]
+ * (n_cols_m x k, ld = k) is copied into one of two batch-owned device buffer
+ * sets on an internal copy-in stream, the batched launch runs on `stream` once
+ * that copy is in, and every member's C (n_rows_m x k) is copied back to
+ * C_host[m] (ld = k) on an internal copy-out stream.  Steps alternate between
+ * the two sets (each with its own member table and graph), so the copy-in of
+ * step i+1 and the copy-out of step i-1 run while step i computes.  Copies of
+ * consecutive members whose host blocks follow one another are merged.  The
+ * sets are allocated on the first call (the operands of spmv_batch_set_io are
+ * not used or changed).  Host arrays B_host[count], C_host[count] are read
+ * during the call; the buffers they point to must stay valid until
+ * spmv_batch_host_sync returns. */
+spmv_status spmv_batch_apply_host_async(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
+                                        void* stream);
+
+/* Wait for every step enqueued by spmv_batch_apply_host_async on this batch. */
+spmv_status spmv_batch_host_sync(spmv_batch_handle b);
+
 /* Same work as separate launches: one kernel per member, in member order (the
  * baseline the batched launch replaces).  Asynchronous. */
 spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream);

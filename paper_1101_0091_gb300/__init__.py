@@ -27,7 +27,8 @@ from ._binding import (SpmvError, VARIANT_NAMES, load, spmv_apply, spmv_apply_bl
 from ._binding_batch import (AUTOTUNE_GRID, POLICY_NAMES, SPMV_BATCH_ADAPT, SPMV_BATCH_L1,  # noqa: F401,E402
                              SPMV_BATCH_L2, SPMV_BATCH_L4, SPMV_BATCH_L8, SPMV_BATCH_L32, SPMV_BATCH_N_POLICIES,
                              SPMV_BATCH_SORTED,
-                             Batch, spmv_batch_apply, spmv_batch_apply_host, spmv_batch_apply_noalloc,
+                             Batch, spmv_batch_apply, spmv_batch_apply_host, spmv_batch_apply_host_async,
+                             spmv_batch_apply_noalloc, spmv_batch_host_sync,
                              spmv_batch_apply_separate,
                              spmv_batch_autotune,
                              spmv_batch_config, spmv_batch_create, spmv_batch_default_config, spmv_batch_destroy,

@@ -27,6 +27,8 @@ _SIGS = {
     "spmv_batch_set_io": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "spmv_batch_apply": ([_vp, _vp], ctypes.c_int),
     "spmv_batch_apply_host": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_batch_apply_host_async": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "spmv_batch_host_sync": ([_vp], ctypes.c_int),
     "spmv_batch_apply_separate": ([_vp, _vp], ctypes.c_int),
     "spmv_batch_set_config": ([_vp, _P(spmv_batch_config)], ctypes.c_int),
     "spmv_batch_get_config": ([_vp, _P(spmv_batch_config)], ctypes.c_int),
@@ -127,6 +129,17 @@ def spmv_batch_apply_host(b, B_host_ptrs, C_host_ptrs, stream) -> None:
     _check(_lib().spmv_batch_apply_host(b, bp, cp, stream))
 
 
+def spmv_batch_apply_host_async(b, B_host_ptrs, C_host_ptrs, stream) -> None:
+    n = len(B_host_ptrs)
+    bp = (ctypes.c_void_p * n)(*B_host_ptrs)
+    cp = (ctypes.c_void_p * n)(*C_host_ptrs)
+    _check(_lib().spmv_batch_apply_host_async(b, bp, cp, stream))
+
+
+def spmv_batch_host_sync(b) -> None:
+    _check(_lib().spmv_batch_host_sync(b))
+
+
 class Batch:
     """Owns one spmv_batch_handle over existing Plans (which must outlive it)."""
 
@@ -151,6 +164,16 @@ class Batch:
         from . import _stream_handle
         spmv_batch_apply_host(self.handle, [_host_ptr(b) for b in B_host], [_host_ptr(c) for c in C_host],
                               _stream_handle(stream))
+
+    def apply_host_async(self, B_host, C_host, stream=None) -> None:
+        """spmv_batch_apply_host_async: one pipelined step from page-locked host
+        blocks (ld = k); the buffers must stay valid until host_sync()."""
+        from . import _stream_handle
+        spmv_batch_apply_host_async(self.handle, [_host_ptr(b) for b in B_host], [_host_ptr(c) for c in C_host],
+                                    _stream_handle(stream))
+
+    def host_sync(self) -> None:
+        spmv_batch_host_sync(self.handle)
 
     def apply_separate(self, stream=None) -> None:
         from . import _stream_handle

@@ -204,6 +204,20 @@ struct spmv_batch_plan {
   // recorded on the caller's stream after every replay: set_io waits on it
   // before it rewrites the member table a replay in flight may still read
   cudaEvent_t ev_last = nullptr;
+  // pipelined host path: two device buffer sets, each with its own member table
+  // and graph; copy-in and copy-out streams; events per set
+  struct Pipe {
+    double* B[2] = {nullptr, nullptr};
+    double* C[2] = {nullptr, nullptr};
+    BatchMat* mats[2] = {nullptr, nullptr};
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t in_done[2] = {nullptr, nullptr}, kern_done[2] = {nullptr, nullptr}, out_done[2] = {nullptr, nullptr};
+    std::vector<int64_t> b_off, c_off;  // member offsets (doubles) inside a set
+    bool vec = false;
+    int64_t step = 0;
+  } pipe;
   bool io_set = false;
   bool vec = false;  // 16-byte loads/stores of right-hand-side rows
   // length-sorted SELL copy of the sorted-policy members (rebuilt when the policies change)
@@ -263,29 +277,44 @@ static void free_graph(spmv_batch_plan* b) {
   b->graph = nullptr;
 }
 
-// Graph of one batched product: counter reset + persistent kernel (the
-// rows-only variant when the list holds no sorted chunks).
-static spmv_status build_graph(spmv_batch_plan* b) {
-  free_graph(b);
+// Graph of one batched product over member table `mats`: counter reset +
+// persistent kernel (the rows-only variant when the list holds no sorted chunks).
+static spmv_status capture_graph(spmv_batch_plan* b, BatchMat* mats, bool vec, cudaGraph_t* graph,
+                                 cudaGraphExec_t* exec) {
   int grid = b->num_sms * b->cfg.ctas_per_sm;
   int dynamic = b->cfg.schedule ? 1 : 0;
   int n_items = (int)b->n_items;
   int k = b->k;
-  void* a_all[] = {(void*)&b->d_mats, (void*)&b->d_items,   (void*)&n_items, (void*)&b->d_rowlist,
-                   (void*)&b->sell,   (void*)&b->d_counter, (void*)&dynamic, (void*)&k};
-  void* a_rows[] = {(void*)&b->d_mats,    (void*)&b->d_items, (void*)&n_items, (void*)&b->d_rowlist,
+  void* a_all[] = {(void*)&mats,    (void*)&b->d_items,   (void*)&n_items, (void*)&b->d_rowlist,
+                   (void*)&b->sell, (void*)&b->d_counter, (void*)&dynamic, (void*)&k};
+  void* a_rows[] = {(void*)&mats,         (void*)&b->d_items, (void*)&n_items, (void*)&b->d_rowlist,
                     (void*)&b->d_counter, (void*)&dynamic,    (void*)&k};
   const bool chunks = b->n_chunk_items > 0;
   SPMV_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
-  cudaError_t e2 = cudaLaunchKernel(chunks ? batch_kernel(b->k, b->vec) : batch_rows_kernel(b->k, b->vec),
-                                    dim3(grid), dim3(kThreads), chunks ? a_all : a_rows, 0, b->cap_stream);
-  cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
+  cudaError_t e2 = cudaLaunchKernel(chunks ? batch_kernel(b->k, vec) : batch_rows_kernel(b->k, vec), dim3(grid),
+                                    dim3(kThreads), chunks ? a_all : a_rows, 0, b->cap_stream);
+  cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, graph);
   if (e1 != cudaSuccess) return cuda_fail(e1, "graph memset node");
   if (e2 != cudaSuccess) return cuda_fail(e2, "graph kernel node");
   if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamEndCapture");
-  SPMV_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  SPMV_CUDA(cudaGraphInstantiate(exec, *graph, 0));
   return SPMV_OK;
+}
+
+static void free_pipe_graphs(spmv_batch_plan* b) {
+  for (int s = 0; s < 2; ++s) {
+    if (b->pipe.exec[s]) cudaGraphExecDestroy(b->pipe.exec[s]);
+    if (b->pipe.graph[s]) cudaGraphDestroy(b->pipe.graph[s]);
+    b->pipe.exec[s] = nullptr;
+    b->pipe.graph[s] = nullptr;
+  }
+}
+
+static spmv_status build_graph(spmv_batch_plan* b) {
+  free_graph(b);
+  free_pipe_graphs(b);  // the pipelined path captures its own again on its next step
+  return capture_graph(b, b->d_mats, b->vec, &b->graph, &b->exec);
 }
 
 // (Re)build the work list and the graph.
@@ -325,6 +354,72 @@ static spmv_status check_config(const spmv_batch_config* c) {
   if (c->schedule != 0 && c->schedule != 1) return fail(SPMV_ERR_ARG, "schedule must be 0 or 1");
   if (c->ctas_per_sm < 1 || c->ctas_per_sm > 8) return fail(SPMV_ERR_ARG, "ctas_per_sm out of range 1..8");
   return SPMV_OK;
+}
+
+// Set up the pipelined host path on first use: two device sets of every
+// member's B and C back to back (ld = k), a member table and a graph per set,
+// the copy streams and the events.
+static spmv_status pipe_setup(spmv_batch_plan* b) {
+  auto& q = b->pipe;
+  const size_t n = b->plans.size();
+  if (q.b_off.empty()) {
+    q.b_off.assign(n + 1, 0);
+    q.c_off.assign(n + 1, 0);
+    for (size_t m = 0; m < n; ++m) {
+      q.b_off[m + 1] = q.b_off[m] + plan_csr(b->plans[m])->n_cols * b->k;
+      q.c_off[m + 1] = q.c_off[m] + b->h_mats[m].n_rows * b->k;
+    }
+    SPMV_CUDA(cudaStreamCreateWithFlags(&q.in, cudaStreamNonBlocking));
+    SPMV_CUDA(cudaStreamCreateWithFlags(&q.out, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+      SPMV_CUDA(cudaMalloc(&q.B[s], sizeof(double) * (size_t)std::max<int64_t>(q.b_off[n], 2)));
+      SPMV_CUDA(cudaMalloc(&q.C[s], sizeof(double) * (size_t)std::max<int64_t>(q.c_off[n], 2)));
+      SPMV_CUDA(cudaMalloc(&q.mats[s], sizeof(BatchMat) * n));
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.in_done[s], cudaEventDisableTiming));
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.kern_done[s], cudaEventDisableTiming));
+      SPMV_CUDA(cudaEventCreateWithFlags(&q.out_done[s], cudaEventDisableTiming));
+      std::vector<BatchMat> t(b->h_mats);
+      for (size_t m = 0; m < n; ++m) {
+        t[m].B = q.B[s] + q.b_off[m];
+        t[m].C = q.C[s] + q.c_off[m];
+        t[m].ldb = b->k;
+        t[m].ldc = b->k;
+      }
+      SPMV_CUDA(cudaMemcpy(q.mats[s], t.data(), sizeof(BatchMat) * n, cudaMemcpyHostToDevice));
+    }
+    // every member's block starts at a multiple of k doubles from a 256-byte aligned base
+    q.vec = b->k % 2 == 0;
+  }
+  for (int s = 0; s < 2; ++s)
+    if (!q.exec[s]) {
+      spmv_status st = capture_graph(b, q.mats[s], q.vec, &q.graph[s], &q.exec[s]);
+      if (st != SPMV_OK) return st;
+    }
+  return SPMV_OK;
+}
+
+// Copies of consecutive members whose host blocks follow one another merge
+// into one copy (the device blocks of a set are back to back).
+template <class DevOf, class HostOf, class LenOf>
+static cudaError_t copy_members(size_t n, DevOf dev_of, HostOf host_of, LenOf len_of, bool to_device,
+                                cudaStream_t s) {
+  size_t m = 0;
+  while (m < n) {
+    if (len_of(m) == 0) {
+      ++m;
+      continue;
+    }
+    char* d = (char*)dev_of(m);
+    char* h = (char*)host_of(m);
+    size_t bytes = len_of(m), e = m + 1;
+    while (e < n && len_of(e) > 0 && (char*)host_of(e) == h + bytes && (char*)dev_of(e) == d + bytes)
+      bytes += len_of(e++);
+    cudaError_t err = to_device ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s)
+                                : cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+    if (err != cudaSuccess) return err;
+    m = e;
+  }
+  return cudaSuccess;
 }
 
 extern "C" {
@@ -478,6 +573,51 @@ spmv_status spmv_batch_apply_host(spmv_batch_handle b, const double* const* B_ho
   return SPMV_OK;
 }
 
+spmv_status spmv_batch_apply_host_async(spmv_batch_handle b, const double* const* B_host, double* const* C_host,
+                                        void* stream) {
+  if (!b || !B_host || !C_host) return fail(SPMV_ERR_ARG, "NULL argument");
+  const size_t n = b->plans.size();
+  for (size_t m = 0; m < n; ++m)
+    if ((plan_csr(b->plans[m])->n_cols > 0 && !B_host[m]) || (b->h_mats[m].n_rows > 0 && !C_host[m]))
+      return fail(SPMV_ERR_ARG, "NULL host buffer of member " + std::to_string(m));
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != b->device) SPMV_CUDA(cudaSetDevice(b->device));
+  spmv_status st = pipe_setup(b);
+  if (st != SPMV_OK) return st;
+  auto& q = b->pipe;
+  const int s = (int)(q.step & 1);
+  cudaStream_t ks = (cudaStream_t)stream;
+  const size_t kb = sizeof(double) * (size_t)b->k;
+  // set s is free for new B once the launch two steps back has read it
+  SPMV_CUDA(cudaStreamWaitEvent(q.in, q.kern_done[s], 0));
+  SPMV_CUDA(copy_members(
+      n, [&](size_t m) { return (void*)(q.B[s] + q.b_off[m]); }, [&](size_t m) { return (void*)B_host[m]; },
+      [&](size_t m) { return kb * (size_t)plan_csr(b->plans[m])->n_cols; }, true, q.in));
+  SPMV_CUDA(cudaEventRecord(q.in_done[s], q.in));
+  // the launch waits for its B and for the copy-out of the step that last used C of set s
+  SPMV_CUDA(cudaStreamWaitEvent(ks, q.in_done[s], 0));
+  SPMV_CUDA(cudaStreamWaitEvent(ks, q.out_done[s], 0));
+  SPMV_CUDA(cudaGraphLaunch(q.exec[s], ks));
+  SPMV_CUDA(cudaEventRecord(q.kern_done[s], ks));
+  SPMV_CUDA(cudaEventRecord(b->ev_last, ks));
+  SPMV_CUDA(cudaStreamWaitEvent(q.out, q.kern_done[s], 0));
+  SPMV_CUDA(copy_members(
+      n, [&](size_t m) { return (void*)(q.C[s] + q.c_off[m]); }, [&](size_t m) { return (void*)C_host[m]; },
+      [&](size_t m) { return kb * (size_t)b->h_mats[m].n_rows; }, false, q.out));
+  SPMV_CUDA(cudaEventRecord(q.out_done[s], q.out));
+  ++q.step;
+  if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_host_sync(spmv_batch_handle b) {
+  if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
+  if (b->pipe.in) SPMV_CUDA(cudaStreamSynchronize(b->pipe.in));
+  if (b->pipe.out) SPMV_CUDA(cudaStreamSynchronize(b->pipe.out));
+  return SPMV_OK;
+}
+
 spmv_status spmv_batch_apply_separate(spmv_batch_handle b, void* stream) {
   if (!b) return fail(SPMV_ERR_ARG, "batch is NULL");
   if (!b->io_set) return fail(SPMV_ERR_ARG, "spmv_batch_set_io was not called");
@@ -587,6 +727,20 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b) {
   if (!b) return SPMV_OK;
   cudaDeviceSynchronize();
   free_graph(b);
+  free_pipe_graphs(b);
+  {
+    auto& q = b->pipe;
+    for (int s2 = 0; s2 < 2; ++s2) {
+      if (q.B[s2]) cudaFree(q.B[s2]);
+      if (q.C[s2]) cudaFree(q.C[s2]);
+      if (q.mats[s2]) cudaFree(q.mats[s2]);
+      if (q.in_done[s2]) cudaEventDestroy(q.in_done[s2]);
+      if (q.kern_done[s2]) cudaEventDestroy(q.kern_done[s2]);
+      if (q.out_done[s2]) cudaEventDestroy(q.out_done[s2]);
+    }
+    if (q.in) cudaStreamDestroy(q.in);
+    if (q.out) cudaStreamDestroy(q.out);
+  }
   if (b->ev_last) cudaEventDestroy(b->ev_last);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->d_items) cudaFree(b->d_items);

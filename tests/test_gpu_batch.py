@@ -253,3 +253,44 @@ def test_set_io_waits_for_a_replay_on_a_non_blocking_stream(lib):
         assert e.value.status == 1 and "NULL B" in str(e.value)
     for p in plans:
         p.close()
+
+
+def test_batch_host_async_pipeline(lib):
+    """spmv_batch_apply_host_async: four pipelined steps with new page-locked
+    operands each (copy-in of one step overlapping the launch and copy-out of
+    its neighbours), members scattered over separate host buffers and members
+    back to back in one; every step's C equals the oracle, bit for bit the
+    device path's result on the same B."""
+    import torch
+    As = members(14, seed=6)
+    plans = [lib.Plan.from_csr(A) for A in As]
+    stream = torch.cuda.Stream()
+    steps = [operands(As, seed=30 + i) for i in range(4)]
+    with lib.Batch(plans, K) as b:
+        pinB = [[torch.from_numpy(B).pin_memory() for B in Bs] for Bs in steps]
+        pinC = [[torch.full((A.n_rows, K), float("nan"), dtype=torch.float64).pin_memory() for A in As]
+                for _ in steps]
+        for i in range(len(steps)):
+            b.apply_host_async(pinB[i], pinC[i], stream)
+        b.host_sync()
+        for Bs, Cs in zip(steps, pinC):
+            check(As, Bs, [C.numpy() for C in Cs])
+        # the same products through the device path agree bit for bit
+        Bd = [dev(B) for B in steps[2]]
+        Cd = [torch.full((A.n_rows, K), float("nan"), dtype=torch.float64, device="cuda") for A in As]
+        b.set_io(Bd, Cd)
+        b.apply(stream)
+        stream.synchronize()
+        for C, Cp in zip(Cd, pinC[2]):
+            assert np.array_equal(host(C), Cp.numpy())
+        # members back to back in one pinned allocation (merged copies), after a configuration change
+        b.set_config(item_nnz=512)
+        nb, nc = [A.n_cols * K for A in As], [A.n_rows * K for A in As]
+        Bf = torch.from_numpy(np.concatenate([B.ravel() for B in steps[3]])).pin_memory()
+        Cf = torch.full((sum(nc),), float("nan"), dtype=torch.float64).pin_memory()
+        b.apply_host_async(list(torch.split(Bf, nb)), list(torch.split(Cf, nc)), stream)
+        b.host_sync()
+        for C, Cp in zip(pinC[3], torch.split(Cf, nc)):
+            assert np.array_equal(Cp.numpy().reshape(C.shape), C.numpy())
+    for p in plans:
+        p.close()
