@@ -51,11 +51,23 @@ def test_poisson280_staged_and_split(lib, poisson280):
     with lib.Plan.from_csr(A, halo_begin=h) as p:
         Bd = dev(B)
         C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
-        p.apply(Bd, C)
+        p.apply(Bd, C)                         # the plan's default kernel (CRS_L1 on this stencil)
         p.check()
         y = host(C)
-        assert not np.isnan(y).any()
+        assert p.info().variant == lib.SPMV_CRS_L1 and not np.isnan(y).any()
         check_sampled(y, A, B, rows)
+        # CRS_STAGED (bulk copies of each row block's tile + mbarrier) on every row: the whole
+        # product against the oracle's loop, and bit for bit against CRS_L1 where rows are short
+        p.set_variant(lib.SPMV_CRS_STAGED)
+        C.fill_(float("nan"))
+        p.apply(Bd, C)
+        p.check()
+        ys = host(C)
+        assert not np.isnan(ys).any()
+        ref = oracle.spmv(A, B)
+        assert oracle.max_err_ratio(ys, ref, oracle.abs_scale(A, B), TOL_FP64) <= 1.0
+        assert np.array_equal(ys, y)           # thread per row in both: the same summation order
+        p.set_variant(lib.SPMV_CRS_L1)
         # split product with the halo copied from pinned host memory on a side stream
         halo = torch.from_numpy(B[h:].copy()).pin_memory()
         Bd[h:] = float("nan")
