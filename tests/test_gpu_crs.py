@@ -361,3 +361,70 @@ def test_zero_initialised_options_build_the_default_plan(lib):
     assert infos[0][1:4] == (0, 0, 0)            # FP64 values, no split
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     assert_close(outs[0], A, gen.uniform(A.n_cols, seed=3))
+
+
+def test_auto_sell_plan_forms(lib):
+    """A plan whose AUTO kernel is SELL-32-256 (scattered gathers) through every
+    product form: k-column blocks with ld > k and an 8-byte offset, FP32-stored
+    values (2e-7 against the FP64 oracle, 1e-13 against its FP32-value loop),
+    and the local/halo split (the local pass runs CRS_L1)."""
+    import torch
+    A = case("eigen")
+    with lib.Plan.from_csr(A) as p:
+        assert p.info().variant == lib.SPMV_SELL
+        for k in (1, 3, 4, 16):
+            ld = k + 3
+            Bh = gen.rhs_block(A.n_cols, k, seed=20 + k)
+            Bbuf = torch.zeros(A.n_cols * ld + 1, dtype=torch.float64, device="cuda")
+            Bv = Bbuf[1:].view(A.n_cols, ld)              # 8 bytes off 16-byte alignment
+            Bv[:, :k] = torch.from_numpy(Bh).cuda()
+            Cbuf = torch.full((A.n_rows * ld + 1,), float("nan"), dtype=torch.float64, device="cuda")
+            Cv = Cbuf[1:].view(A.n_rows, ld)
+            p.apply_block(Bv, Cv, k)
+            p.check()
+            y = host(Cv)
+            assert_close(y[:, :k], A, Bh)
+            assert np.isnan(y[:, k:]).all()                 # nothing beyond the k columns is written
+    B = gen.uniform(A.n_cols, seed=21)
+    with lib.Plan.from_csr(A, val_fp32=True) as p:
+        assert p.info().variant == lib.SPMV_SELL
+        y = run(p, B)
+        assert_close(y, A, B, tol=TOL_FP32VAL)
+        assert_close(y, A, B, f32val=True)
+    h = A.n_cols - A.n_cols // 7
+    with lib.Plan.from_csr(A, halo_begin=h) as p:
+        assert p.info().variant == lib.SPMV_SELL
+        Bd = dev(B)
+        halo = torch.from_numpy(B[h:].copy()).pin_memory()
+        Bd[h:] = float("nan")
+        C = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        p.apply_split(Bd, halo, C, torch.cuda.current_stream(), torch.cuda.Stream())
+        p.check()
+        assert_close(host(C), A, B)
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (0, 5), (5, 0), (1, 1), (2, 7), (3, 3)])
+def test_auto_tiny_and_empty_shapes(lib, shape):
+    """AUTO's row sample on matrices too small to sample (fewer than three
+    rows) or without entries: the plan builds on CRS_L1 (a zero scattered
+    share where nothing is sampled; where something is, SELL-32-256 fills too
+    few of its slots here to be chosen), and the product is the oracle's."""
+    n, m = shape
+    rng = np.random.default_rng(n * 10 + m)
+    rp = np.zeros(n + 1, np.int32)
+    cols, vals = [], []
+    for i in range(n):
+        c = np.sort(rng.choice(m, size=min(m, 2), replace=False)) if m else np.zeros(0, np.int64)
+        cols.append(c)
+        vals.append(rng.integers(-5, 6, len(c)).astype(np.float64))
+        rp[i + 1] = rp[i] + len(c)
+    A = gen.CSR(n, m, rp, np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32),
+                np.concatenate(vals) if vals else np.zeros(0))
+    with lib.Plan.from_csr(A) as p:
+        i = p.info()
+        assert i.variant == lib.SPMV_CRS_L1
+        if n < 3 or m == 0:
+            assert i.scattered == 0.0
+        if n and m:
+            B = rng.integers(-5, 6, m).astype(np.float64)
+            assert_close(run(p, B), A, B, exact=True)
