@@ -4,7 +4,7 @@
 Default workload: the 3D 7-point variable-coefficient Poisson stencil on a
 280^3 grid (N = 21,952,000 rows, 153,193,600 nonzeros, FP64 CRS), the stand-in
 for the paper's sAMG matrix.  One step = one product C = A*B with the plan's
-default kernel (CRS_L1: thread per row; the val/col slices of the CTA 152
+default kernel (CRS_L1: thread per row; the val/col slices of the CTA 456
 positions ahead are prefetched into L2 by the TMA engine).  Inputs (2.28 GB)
 exceed L2 (129 MB), so no flush is needed between steps.
 

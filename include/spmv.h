@@ -194,7 +194,7 @@ spmv_status spmv_get_info(spmv_handle h, spmv_info* info);
 /* Launch parameters a tuner may change without touching the result.
  * prefetch_distance: each CTA of the row and SELL kernels asks the TMA engine
  * to prefetch into L2 the matrix slice of the CTA this many positions ahead
- * (cp.async.bulk.prefetch.L2); 0 disables it.  Default: 152 (one per SM), and
+ * (cp.async.bulk.prefetch.L2); 0 disables it.  Default: 456 (three per SM), and
  * 0 on matrices whose gathers are scattered (the test of SPMV_VARIANT_AUTO):
  * their product is bound by the SMs' requests to L2, which a prefetch adds
  * to. */

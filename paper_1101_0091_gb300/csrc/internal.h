@@ -79,6 +79,12 @@ bool validate_permutation(int64_t n, const int32_t* perm, std::vector<int32_t>* 
 // A' = P A P^T: row r of A' is row perm[r] of A, columns relabelled by inv and sorted (stable).
 void permute_csr(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, const int32_t* perm,
                  const std::vector<int32_t>& inv, int32_t* out_row_ptr, int32_t* out_col, double* out_val);
+// Default L2 prefetch distance of the row and SELL kernels, in CTAs ahead:
+// three per SM.  280^3 Poisson product, CRS_L1: 0 / 76 / 152 / 228 / 304 /
+// 456 / 608 CTAs ahead gave 871 / 917 / 926 / 930 / 933 / 933.5 / 933.7
+// GFlop/s.
+constexpr int kDefaultPrefetch = 456;
+
 // AUTO: a matrix whose sampled entries are scattered beyond this share (see
 // scattered_fraction) runs without the L2 prefetch, and runs SELL-32-256 when
 // that format stores at least kAutoSellFill nonzeros per slot.

@@ -19,7 +19,6 @@ constexpr int kLongRow = 64;         // rows longer than this are handled warp-p
 constexpr int kWarpRowsPerBlock = kThreads / 32;
 constexpr int kSellC = 32;           // SELL chunk height
 constexpr uint32_t kBlockWarpFlag = 0x80000000u;  // high bit of a row-block entry: warp-per-row block
-constexpr int kDefaultPrefetch = 152;  // default L2 prefetch distance (CTAs ahead; one per SM)
 
 // Device view of one CRS matrix (values in FP64 and, optionally, FP32).
 struct CsrDev {

@@ -210,7 +210,7 @@ def test_set_variant_switches(lib):
     B = gen.uniform(A.n_cols, seed=4)
     with lib.Plan.from_csr(A) as p:
         assert p.info().variant == lib.SPMV_CRS_L1   # the default (AUTO) kernel
-        assert p.tuning().prefetch_distance == 152
+        assert p.tuning().prefetch_distance == 456   # three CTAs per SM ahead
         for _, vid, sig in VARIANTS:
             p.set_variant(vid, sig)
             assert p.info().variant == vid
@@ -232,7 +232,7 @@ def test_auto_variant_follows_the_gather_pattern(lib, name, scattered):
         if scattered:
             assert (i.variant, i.sell_sigma, t.prefetch_distance) == (lib.SPMV_SELL, 256, 0)
         else:
-            assert (i.variant, t.prefetch_distance) == (lib.SPMV_CRS_L1, 152)
+            assert (i.variant, t.prefetch_distance) == (lib.SPMV_CRS_L1, 456)
         assert_close(run(p, B), A, B, exact=(name == "integer"))
 
 
