@@ -385,11 +385,10 @@ spmv_status spmv_batch_destroy(spmv_batch_handle b);
  * the work list.  Limits: count <= 8192 members and at most 245,752 work
  * items (one item per 32 warp passes: 1024 rows at 1 lane per row), beyond
  * which the call returns SPMV_ERR_ARG without touching the device.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call clears the
- * counter and overwrites the table and the list in the shared array, so calls
- * that overlap on the GPU (other streams, other host threads) race: order them
- * on one stream.  Host calls are serialised by a mutex.  Asynchronous on
+ * call on a device looks up the array's device address (cudaGetSymbolAddress).
+ * Every call clears the counter and overwrites the table and the list in the
+ * shared array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: order them on one stream.  Host calls are serialised by a mutex.  Asynchronous on
  * `stream`; calls no cudaMalloc, cudaFree or allocating library routine. */
 spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_rows, const int32_t* const* row_ptr_dev,
                                      const int32_t* const* col_dev, const double* const* val_dev,

@@ -42,6 +42,11 @@ struct BatchSell {
   const double* val;
 };
 
+// C is written once per product: streaming (evict-first) stores leave L2 to
+// the B blocks of the members in flight.
+__device__ __forceinline__ void st_c(double* p, double x) { __stcs(p, x); }
+__device__ __forceinline__ void st_c(double2* p, double2 x) { __stcs(p, x); }
+
 // 16-byte loads of two consecutive right-hand-side values when B rows are
 // 16-byte aligned (VEC), else single 8-byte loads.
 template <int K, bool VEC>
@@ -124,11 +129,11 @@ __device__ __forceinline__ void batch_rows(const BatchMat* __restrict__ Mp, cons
       if (VEC && L == 1 && K >= 2) {
 #pragma unroll
         for (int q = 0; q + 1 < K; q += 2)
-          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+          if (q < k) st_c(reinterpret_cast<double2*>(out + q), make_double2(acc[q], acc[q + 1]));
       } else {
 #pragma unroll
         for (int q = 0; q < K; ++q)
-          if (q < k && (L == 1 || t == q % L)) out[q] = acc[q];
+          if (q < k && (L == 1 || t == q % L)) st_c(out + q, acc[q]);
       }
     }
   }
@@ -176,11 +181,11 @@ __device__ __forceinline__ int chunks_fixed(const BatchMat* __restrict__ Mp, con
       if (VEC && K >= 2) {
 #pragma unroll
         for (int q = 0; q + 1 < K; q += 2)
-          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+          if (q < k) st_c(reinterpret_cast<double2*>(out + q), make_double2(acc[q], acc[q + 1]));
       } else {
 #pragma unroll
         for (int q = 0; q < K; ++q)
-          if (q < k) out[q] = acc[q];
+          if (q < k) st_c(out + q, acc[q]);
       }
     }
   }
@@ -251,11 +256,11 @@ __device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, co
       if (VEC && K >= 2) {
 #pragma unroll
         for (int q = 0; q + 1 < K; q += 2)
-          if (q < k) *reinterpret_cast<double2*>(out + q) = make_double2(acc[q], acc[q + 1]);
+          if (q < k) st_c(reinterpret_cast<double2*>(out + q), make_double2(acc[q], acc[q + 1]));
       } else {
 #pragma unroll
         for (int q = 0; q < K; ++q)
-          if (q < k) out[q] = acc[q];
+          if (q < k) st_c(out + q, acc[q]);
       }
     }
   }
