@@ -274,11 +274,11 @@ typedef enum {
 typedef struct {
   int32_t item_nnz;       /* target nonzeros per work item (64 .. 1<<20)              */
   int32_t schedule;       /* 0 = static round-robin over warps, 1 = atomic counter     */
-  int32_t ctas_per_sm;    /* persistent grid = SMs x ctas_per_sm (1 .. 8)              */
+  int32_t ctas_per_sm;    /* persistent grid = SMs x ctas_per_sm CTAs of 128 threads (1 .. 8); 7 stay resident */
   int32_t reserved[5];
 } spmv_batch_config;
 
-/* Default batch configuration: item_nnz 1024, atomic counter, 8 CTAs per SM. */
+/* Default batch configuration: item_nnz 1024, atomic counter, 7 CTAs per SM. */
 spmv_batch_config spmv_batch_default_config(void);
 
 /* Build a batch over `count` plans (same device) with k right-hand sides each
@@ -347,7 +347,7 @@ spmv_status spmv_batch_get_config(spmv_batch_handle b, spmv_batch_config* cfg);
 spmv_status spmv_batch_set_policies(spmv_batch_handle b, const int32_t* policies);
 
 /* Autotuner: times every configuration of item_nnz in {256, 512, 1024, 2048,
- * 4096} x schedule in {static, atomic} x ctas_per_sm in {4, 8} (`reps` graph
+ * 4096} x schedule in {static, atomic} x ctas_per_sm in {4, 7} (`reps` graph
  * replays each after one warm-up, CUDA events on `stream`; needs set_io
  * first), keeps the fastest, and returns it (best may be NULL).  times_ms
  * (NULL or 20 entries) receives the median time of each configuration in that

@@ -12,7 +12,7 @@ from ._binding import _check, _i32, _i64, _vp, load
 SPMV_BATCH_L1, SPMV_BATCH_L2, SPMV_BATCH_L4, SPMV_BATCH_L8, SPMV_BATCH_L32, SPMV_BATCH_ADAPT, SPMV_BATCH_SORTED = range(7)
 SPMV_BATCH_N_POLICIES = 7
 POLICY_NAMES = {0: "l1", 1: "l2", 2: "l4", 3: "l8", 4: "l32", 5: "adapt", 6: "sorted"}
-AUTOTUNE_GRID = [(item, sched, ctas) for item in (256, 512, 1024, 2048, 4096) for sched in (0, 1) for ctas in (4, 8)]
+AUTOTUNE_GRID = [(item, sched, ctas) for item in (256, 512, 1024, 2048, 4096) for sched in (0, 1) for ctas in (4, 7)]
 
 
 class spmv_batch_config(ctypes.Structure):

@@ -293,7 +293,7 @@ static spmv_status capture_graph(spmv_batch_plan* b, BatchMat* mats, bool vec, c
   SPMV_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
   cudaError_t e2 = cudaLaunchKernel(chunks ? batch_kernel(b->k, vec) : batch_rows_kernel(b->k, vec), dim3(grid),
-                                    dim3(kThreads), chunks ? a_all : a_rows, 0, b->cap_stream);
+                                    dim3(kBatchThreads), chunks ? a_all : a_rows, 0, b->cap_stream);
   cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, graph);
   if (e1 != cudaSuccess) return cuda_fail(e1, "graph memset node");
   if (e2 != cudaSuccess) return cuda_fail(e2, "graph kernel node");
@@ -429,7 +429,7 @@ spmv_batch_config spmv_batch_default_config(void) {
   std::memset(&c, 0, sizeof(c));
   c.item_nnz = 1024;
   c.schedule = 1;
-  c.ctas_per_sm = 8;
+  c.ctas_per_sm = kBatchCtasPerSm;
   return c;
 }
 
@@ -659,7 +659,7 @@ spmv_status spmv_batch_autotune(spmv_batch_handle b, void* stream, int32_t reps,
   cudaStream_t s = (cudaStream_t)stream;
   const int item_opts[5] = {256, 512, 1024, 2048, 4096};
   const int sched_opts[2] = {0, 1};
-  const int cta_opts[2] = {4, 8};
+  const int cta_opts[2] = {4, kBatchCtasPerSm};
   cudaEvent_t e0, e1;
   SPMV_CUDA(cudaEventCreate(&e0));
   SPMV_CUDA(cudaEventCreate(&e1));

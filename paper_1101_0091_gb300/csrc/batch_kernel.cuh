@@ -266,6 +266,18 @@ __device__ __forceinline__ void batch_chunks(const BatchMat* __restrict__ Mp, co
   }
 }
 
+// Threads per CTA of the persistent kernels, and the CTAs per SM the register
+// budget is sized for: for k <= 4 at 72 registers seven 128-thread CTAs (28
+// warps) stay resident (256-thread CTAs held to 64 registers spilled, and only
+// three of them fitted on an SM, not four: 24 warps); the wider gathers of
+// k = 8 / 16 keep about 100 registers (four or five CTAs) rather than spill.
+constexpr int kBatchThreads = 128;
+constexpr int kBatchCtasPerSm = 7;
+template <int K>
+struct BatchMinCtas {
+  static constexpr int value = K <= 4 ? kBatchCtasPerSm : 4;
+};
+
 // Persistent kernel: warps take items round-robin (dynamic = 0) or from the
 // atomic counter (dynamic = 1, counter zeroed before the launch).
 // Next item index of the calling warp: round-robin or from the atomic counter.
@@ -278,12 +290,12 @@ __device__ __forceinline__ int next_item(int it, int nw, int dynamic, int* count
 
 // Persistent kernel over row items (modes 0-2).
 template <int K, bool VEC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBatchThreads, BatchMinCtas<K>::value)
     k_batch_rows(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
                  const int2* __restrict__ rowlist, int* __restrict__ counter, int dynamic, int k) {
   const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (kThreads / 32);
+  const int wid = blockIdx.x * (kBatchThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (kBatchThreads / 32);
   int it = dynamic ? next_item(0, nw, 1, counter, lane) : wid;
   while (it < n_items) {
     const BatchItem item = items[it];
@@ -304,12 +316,12 @@ __global__ void __launch_bounds__(kThreads)
 // gathered while it is resident in L2 (two separate kernels, one per mode,
 // would stream every B block twice).
 template <int K, bool VEC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBatchThreads, BatchMinCtas<K>::value)
     k_batch(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items, int n_items,
             const int2* __restrict__ rowlist, BatchSell sell, int* __restrict__ counter, int dynamic, int k) {
   const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (kThreads / 32);
+  const int wid = blockIdx.x * (kBatchThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (kBatchThreads / 32);
   int it = dynamic ? next_item(0, nw, 1, counter, lane) : wid;
   while (it < n_items) {
     const BatchItem item = items[it];

@@ -111,6 +111,7 @@ extern "C" spmv_status spmv_batch_apply_noalloc(int32_t count, const int64_t* n_
   int ni = (int)n_items, dynamic = 1, kk = k;
   void* args[] = {(void*)&mats, (void*)&ditems, (void*)&ni, (void*)&rowlist, (void*)&counter, (void*)&dynamic,
                   (void*)&kk};
-  SPMV_CUDA(cudaLaunchKernel(batch_rows_kernel(k, vec), dim3(sms * 4), dim3(kThreads), args, 0, s));
+  SPMV_CUDA(cudaLaunchKernel(batch_rows_kernel(k, vec), dim3(sms * kBatchCtasPerSm), dim3(kBatchThreads), args,
+                             0, s));
   return SPMV_OK;
 }
