@@ -104,11 +104,15 @@ def test_batch_configs_same_result(lib, cfg):
             assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("k", [1, 3, 16])
-def test_batch_other_k(lib, k):
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 16])
+@pytest.mark.parametrize("policy", ["adapt", "sorted"])
+def test_batch_other_k(lib, k, policy):
+    """Every width of the kernel (k = 1, 2, 4 for k = 3, 8, 16; each with its
+    own register budget and resident CTAs) against the oracle."""
     As = members(8)
     Bs = operands(As, k=k)
-    check(As, Bs, run_batch(lib, As, Bs, [lib.SPMV_BATCH_ADAPT] * len(As), k=k))
+    pol = lib.SPMV_BATCH_ADAPT if policy == "adapt" else lib.SPMV_BATCH_SORTED
+    check(As, Bs, run_batch(lib, As, Bs, [pol] * len(As), k=k))
 
 
 def test_batch_separate_launches(lib):
