@@ -1054,7 +1054,7 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         Cpin_flat = [torch.empty(sum(nc), dtype=torch.float64).pin_memory() for _ in range(2)]
         Bpin = [list(torch.split(x, nb)) for x in Bpin_flat]
         Cpin = [list(torch.split(x, nc)) for x in Cpin_flat]
-        n_e2e = 8
+        n_e2e = 40  # the pipeline's fill and drain (one copy each way) stay a few percent of the region
         for i in range(2):
             batch.apply_host_async(Bpin[i % 2], Cpin[i % 2], stream)
         batch.host_sync()
