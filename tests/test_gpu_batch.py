@@ -92,7 +92,8 @@ def test_batch_equals_solo_kernel_bitwise(lib, policy, variant):
 @pytest.mark.parametrize("cfg", [dict(item_nnz=64, schedule=0, ctas_per_sm=1),
                                  dict(item_nnz=4096, schedule=1, ctas_per_sm=8),
                                  dict(item_nnz=1 << 20, schedule=0, ctas_per_sm=4),
-                                 dict(item_nnz=300, schedule=1, ctas_per_sm=2)])
+                                 dict(item_nnz=300, schedule=1, ctas_per_sm=2),
+                                 dict(item_nnz=512, schedule=0, ctas_per_sm=8)])   # static, CTAs beyond residency
 def test_batch_configs_same_result(lib, cfg):
     As = members(10)
     Bs = operands(As)

@@ -84,6 +84,18 @@ def test_no_alloc_matches_batch_entry_twice(lib):
     compare(As2, Bs2, lanes2, no_alloc(spmv, As2, Bs2, 3, lanes2), regular(spmv, As2, Bs2, 3, lanes2))
 
 
+@pytest.mark.parametrize("k", [1, 2, 8, 16])
+def test_no_alloc_other_widths(lib, k):
+    """The other kernel widths (each with its own register budget, so fewer
+    of the launched CTAs may be resident at once) against the oracle and the
+    regular entry point."""
+    import paper_1101_0091_gb300 as spmv
+    As = [gen.powerlaw_batch_member(m, seed=5, dim_lo=1e3, dim_hi=2e4) for m in range(6)]
+    Bs = [gen.rhs_block(A.n_cols, k, seed=60 + m) for m, A in enumerate(As)]
+    lanes = [1, 2, 4, 8, 16, 32]
+    compare(As, Bs, lanes, no_alloc(spmv, As, Bs, k, lanes), regular(spmv, As, Bs, k, lanes))
+
+
 def test_no_alloc_rejects_sizes_beyond_the_scratch(lib):
     """Sizes beyond the static scratch and NULL operands are rejected on the
     host before any CUDA call (the pointers below are never dereferenced)."""
