@@ -274,7 +274,9 @@ typedef enum {
 typedef struct {
   int32_t item_nnz;       /* target nonzeros per work item (64 .. 1<<20)              */
   int32_t schedule;       /* 0 = static round-robin over warps, 1 = atomic counter     */
-  int32_t ctas_per_sm;    /* persistent grid = SMs x ctas_per_sm CTAs of 128 threads (1 .. 8); 7 stay resident */
+  int32_t ctas_per_sm;    /* persistent grid = SMs x ctas_per_sm CTAs of 128 threads (1 .. 8); at most 7
+                             resident per SM for k <= 4, 5 for k = 5..8, 4 for k = 9..16 (the static
+                             schedule runs the items of CTAs beyond that after the resident ones) */
   int32_t reserved[5];
 } spmv_batch_config;
 
