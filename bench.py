@@ -359,6 +359,21 @@ def replica_value(units_per_rank: float, seconds_max: float, world: int) -> floa
     return units_per_rank * world / seconds_max
 
 
+SLOWDOWN_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(c) -> bool:
+    """A timed region that saw a hardware or thermal slowdown, or SM clocks
+    well below their maximum with no reason given (a clock lock left by
+    someone), is not a valid measurement; sw_power_cap alone is kept."""
+    if not c or not c.get("samples"):
+        return False
+    if any(r in c.get("reasons", []) for r in SLOWDOWN_REASONS):
+        return True
+    return bool(c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.9 * c["sm_max_mhz"]
+                and not c.get("reasons"))
+
+
 class Timer:
     """CUDA-event timing of `steps` calls on one stream, with a barrier and a
     synchronize on both sides and nvidia-smi clock samples inside the region."""
@@ -401,6 +416,17 @@ class Timer:
         return {"total_ms": total_ms, "per_ms": per, "wall_s": t1 - t0,
                 "clocks": clk.summary(t0, t1) if clk else None}
 
+    def run_checked(self, fn, steps, warmup):
+        """run() with clock samples; a region whose clocks are rejected (on
+        any rank) is measured once more, and the line keeps the first
+        region's clock record beside the second."""
+        r = self.run(fn, steps, warmup, sample_clocks=True)
+        if all_max([1.0 if clocks_rejected(r["clocks"]) else 0.0], self.world)[0] > 0:
+            first = r["clocks"]
+            r = self.run(fn, steps, warmup, sample_clocks=True)
+            r["clocks"] = dict(r["clocks"] or {}, remeasured_after=first)
+        return r
+
 
 def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     import gen
@@ -418,7 +444,7 @@ def single_workload(args, torch, spmv, pm, timer, stream, world, rank):
     tr = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=k, val_bytes=4 if args.fp32_val else 8)
     if vid == spmv.SPMV_SYM:
         tr = pm.gpu_sym_min_traffic(A.n_rows, A.nnz, plan.info().sym_nnz, k=k, val_bytes=4 if args.fp32_val else 8)
-    r = timer.run(fn, args.steps, args.warmup, sample_clocks=True)
+    r = timer.run_checked(fn, args.steps, args.warmup)
     plan.check(stream)
     t_step = r["total_ms"] / 1e3 / args.steps
     kern_s = statistics.mean(r["per_ms"]) / 1e3
@@ -1018,7 +1044,7 @@ def batch_workload(args, torch, spmv, pm, timer, stream, world, rank):
         best, times = batch.autotune(stream, reps=3)
         tuned = {"item_nnz": best.item_nnz, "schedule": ["static", "atomic"][best.schedule],
                  "ctas_per_sm": best.ctas_per_sm}
-    r = timer.run(lambda: batch.apply(stream), args.steps, args.warmup, sample_clocks=True)
+    r = timer.run_checked(lambda: batch.apply(stream), args.steps, args.warmup)
     t_step = r["total_ms"] / 1e3 / args.steps
     kern_s = statistics.mean(r["per_ms"]) / 1e3
     bytes_min = sum(pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, k=4).bytes_min for A in As)
