@@ -594,8 +594,13 @@ def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
         t_ov = med(lambda: ps.apply_split(B, halo, C, stream, cs), 100)
         t_ser = med(lambda: ps.apply_split(B, halo, C, stream, stream), 100)
         info = ps.info()
+        hbm, _ = measured_hbm()
+        # the split's own bound: V_min plus the halo pass's extra bytes at the copy peak
+        t_bound = (tr.bytes_min + pm.gpu_split_extra_bytes(info.n_halo_rows)) / (hbm * 1e9)
         forms["split_overlapped"] = {"gflops": round(tr.flops / t_ov / 1e9, 1), "ms": round(t_ov * 1e3, 4),
-                                     "halo_bytes_h2d": 8 * (A.n_cols - h), "n_halo_rows": info.n_halo_rows}
+                                     "halo_bytes_h2d": 8 * (A.n_cols - h), "n_halo_rows": info.n_halo_rows,
+                                     "bound_gflops": round(tr.flops / t_bound / 1e9, 1),
+                                     "frac_of_bound": round(t_bound / t_ov, 4)}
         forms["split_serial_copy"] = {"gflops": round(tr.flops / t_ser / 1e9, 1), "ms": round(t_ser * 1e3, 4)}
         forms["split_penalty_eq2_model"] = round(pm.split_penalty(A.nnz / A.n_rows), 4)
     return forms
