@@ -584,8 +584,13 @@ def poisson_forms(A, Bh, torch, spmv, pm, timer, stream, plan, B, C):
     with spmv.Plan.from_csr(A, val_fp32=True) as p32:
         t = med(lambda: p32.apply(B, C, stream))
         tr32 = pm.gpu_min_traffic(A.n_rows, A.n_cols, A.nnz, val_bytes=4)
+        hbm, _ = measured_hbm()
+        # 8 streamed bytes per entry instead of 12, and one FP64 FMA per entry: both roofs are close
+        t_b = max(tr32.bytes_min / (hbm * 1e9), tr.flops / (fp64_peak() * 1e9))
         forms["crs_l1_fp32val"] = {"gflops": round(tr.flops / t / 1e9, 1),
-                                   "hbm_gbs": round(tr32.bytes_min / t / 1e9, 1), "err_bound": "2e-7*sum|ab|"}
+                                   "hbm_gbs": round(tr32.bytes_min / t / 1e9, 1), "err_bound": "2e-7*sum|ab|",
+                                   "bound": "max(HBM time of V_min with 4-byte values, FP64 time of the FMAs)",
+                                   "bound_gflops": round(tr.flops / t_b / 1e9, 1), "frac_of_bound": round(t_b / t, 4)}
     # local/halo split: last 10% of the columns copied from pinned host memory on a side stream
     h = A.n_cols - A.n_cols // 10
     with spmv.Plan.from_csr(A, halo_begin=h) as ps:
